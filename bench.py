@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: 3D split-step steps/s and HBM roofline at 256x256x1024.
+
+One bench step = one observation interval of the propagation: SPLIT Strang
+steps of the three-guide workload (ctap_step) followed by the FP64
+observables (norm, energies, guide populations; ctap_observables), the
+paper's per-interval record (Sec. V, Fig. 4).  `value` counts split steps per
+second, whole job.  The FP32 path (complex64 with FP64 tables and
+reductions) is the headline; the FP64 path (complex128) is timed on the same
+workload and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun): the
+propagation does not shard without all-to-all transposes, so the multi-GPU
+mode is a replica sweep, as in the paper's concurrent runs on a second card.
+--impl reference times the FP64 CPU oracle (the test reference) on the
+host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "3D split-step steps/s and HBM roofline % at 256x256x1024, FP32 vs FP64 path"
+SHAPE = (1024, 256, 256)
+DT = 0.0025
+SPLIT = 50                 # split steps per bench step (one observation interval)
+SPLIT_FP64 = 2
+KERNEL_SOURCES = ["device_fft.cuh", "kernels.cuh", "kernels.cu"]
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1309_2451_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_hash") != kernel_hash():
+            return None
+        return d.get(kind)
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the
+    timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_plan(ctap, wl, dtype, stream):
+    box = wl.CTAP_BOX
+    z = wl.axis(SHAPE[0], box[4], box[5])
+    c = wl.guide_centres(z)
+    plan = ctap.Plan(SHAPE, box, dtype, stream=stream)
+    plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    return plan
+
+
+def initial_state(wl, dtype_t, torch, device):
+    """Guide-1 transverse ground state (imaginary time on the nz = 1 plane is
+    skipped here: the bench times propagation) approximated by the seed
+    Gaussian, times the z-packet; seeded and synthetic."""
+    box = wl.CTAP_BOX
+    xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
+    phi = wl.guide_seed_2d(SHAPE[1:], box, xc)
+    psi = wl.packet_from_transverse(phi, SHAPE[0], box)
+    return torch.from_numpy(psi).to(device=device, dtype=dtype_t)
+
+
+def time_path(ctap, wl, torch, dtype, split, steps, warmup, device, stream, profile=True):
+    plan = build_plan(ctap, wl, dtype, stream)
+    t = torch.complex64 if dtype == "c64" else torch.complex128
+    psi = initial_state(wl, t, torch, device)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.step(psi, split, DT)
+            plan.observables(psi)
+    torch.cuda.synchronize()
+    plan.set_profiling(profile)
+    plan.pass_times()
+    launches0 = plan.launch_count
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    obs = None
+    with Clocks(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            plan.step(psi, split, DT)
+            obs = plan.observables(psi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = plan.launch_count - launches0
+    counts, pms = plan.pass_times()
+    plan.set_profiling(False)
+    return dict(plan=plan, psi=psi, ms=ms, launches=launches, counts=counts, pass_ms=pms,
+                obs=obs, clocks=clk.summary())
+
+
+def time_e2e(ctap, wl, torch, steps, device, stream, plan):
+    """Same metric through the public API with host buffers: every bench
+    step copies psi from pinned host memory, propagates, and reads the
+    observables back."""
+    host = initial_state(wl, torch.complex64, torch, "cpu").pin_memory()
+    psi = torch.empty(SHAPE, dtype=torch.complex64, device=device)
+    with torch.cuda.stream(stream):
+        psi.copy_(host, non_blocking=True)
+        plan.step(psi, SPLIT, DT)
+        plan.observables(psi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            psi.copy_(host, non_blocking=True)
+            plan.step(psi, SPLIT, DT)
+            plan.observables(psi)          # synchronising D2H of 6 doubles
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dict(value=steps * SPLIT / dt, unit="steps/s",
+                h2d_bytes_per_step=int(host.numel() * host.element_size()),
+                d2h_bytes_per_step=6 * 8)
+
+
+def cpu_baseline(seconds_cap=30.0):
+    """The FP64 oracle, as it stands, on the host cores: split steps of the
+    full 256x256x1024 workload, as many as fit in about `seconds_cap`."""
+    import oracle
+    from paper_1309_2451_b300 import workloads as wl
+    box = wl.CTAP_BOX
+    z = wl.axis(SHAPE[0], box[4], box[5])
+    c = wl.guide_centres(z)
+    V = oracle.ctap_potential(SHAPE, box, wl.V0, wl.SIGMA_GUIDE, c[0], c[2])
+    xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
+    psi = wl.packet_from_transverse(wl.guide_seed_2d(SHAPE[1:], box, xc), SHAPE[0], box)
+    n, t_total = 0, 0.0
+    while t_total < seconds_cap and n < 10:
+        t0 = time.perf_counter()
+        psi = oracle.step(psi, V, box, DT, 1)
+        t_total += time.perf_counter() - t0
+        n += 1
+        if n == 1 and t_total > seconds_cap / 2:
+            break
+    return {"value": n / t_total, "unit": "steps/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} FP64 split step(s) of the 256x256x1024 three-guide workload "
+                      f"({t_total:.1f} s, OpenMP over lines)"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1309_2451_b300 import workloads as wl
+    box = wl.CTAP_BOX
+    z = wl.axis(SHAPE[0], box[4], box[5])
+    c = wl.guide_centres(z)
+    V = oracle.ctap_potential(SHAPE, box, wl.V0, wl.SIGMA_GUIDE, c[0], c[2])
+    xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
+    psi = wl.packet_from_transverse(wl.guide_seed_2d(SHAPE[1:], box, xc), SHAPE[0], box)
+    # each bench step is a bounded sample of the workload: one FP64 split step
+    for _ in range(a.warmup):
+        psi = oracle.step(psi, V, box, DT, 1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        psi = oracle.step(psi, V, box, DT, 1)
+    el = time.perf_counter() - t0
+    v = a.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1000.0 * el / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ctap_large: 256x256x1024 three-guide split step",
+                       "grid": list(SHAPE[::-1]), "dt": DT,
+                       "bench_step": "one FP64 split step (the oracle, bounded sample)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{a.steps} FP64 split steps of the full workload"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    from paper_1309_2451_b300 import build, ctap, workloads as wl
+    rank, world, local = dist_info()
+    build.build()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    stream = torch.cuda.Stream(device=device)
+
+    if world > 1:
+        dist.barrier()
+    res = time_path(ctap, wl, torch, "c64", SPLIT, a.steps, a.warmup, device, stream)
+    ms = res["ms"]
+    if world > 1:
+        tt = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    split_total = a.steps * SPLIT * world
+    value = split_total / (ms / 1000.0)
+
+    N = int(np.prod(SHAPE))
+    esize = 8
+    hbm, peak_kind = peaks()
+    counts, pms = res["counts"], res["pass_ms"]
+    kind = 0 if pms[0] >= pms[1] else 1
+    name = "xy_pass_kernel" if kind == 0 else "z_pass_kernel"
+    avg_ms = pms[kind] / max(counts[kind], 1)
+    bytes_launch = 2 * N * esize       # one read and one write of psi
+    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": recorded_traffic(name),
+                "kernel": name, "peak_kind": peak_kind,
+                "step_design_GBps": 4 * N * esize * a.steps * SPLIT / (res["ms"] * 1e-3) / 1e9}
+
+    extra = {}
+    if rank == 0 and not a.no_fp64:
+        r64 = time_path(ctap, wl, torch, "c128", SPLIT_FP64, max(2, a.steps // 10), 1, device,
+                        stream)
+        ms64 = r64["ms"] / (max(2, a.steps // 10) * SPLIT_FP64)
+        c64, p64 = r64["counts"], r64["pass_ms"]
+        k64 = 0 if p64[0] >= p64[1] else 1
+        avg64 = p64[k64] / max(c64[k64], 1)
+        ach64 = 2 * N * 16 / (avg64 * 1e-3) / 1e9
+        extra["fp64_path"] = {
+            "steps_per_s": 1000.0 / ms64, "ms_per_step": ms64,
+            "hbm_frac_of_dominant_kernel": ach64 / hbm,
+            "fp32_speedup": (1000.0 / (ms / (a.steps * SPLIT))) / (1000.0 / ms64),
+            "dtype": "f64", "obs": [float(x) for x in r64["obs"]]}
+        del r64
+    if rank == 0 and not a.no_extras:
+        extra["cpu_baseline"] = cpu_baseline()
+    e2e = time_e2e(ctap, wl, torch, max(3, a.steps // 4), device, stream, res["plan"])
+    if world > 1:
+        tt = torch.tensor([e2e["value"]], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MIN)
+        e2e["value"] = float(tt.item()) * world
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "ctap_large: 256x256x1024 three-guide Strang split step, "
+                                       "complex64 bulk, FP64 tables and reductions",
+                           "grid": list(SHAPE[::-1]), "dt": DT,
+                           "split_steps_per_bench_step": SPLIT,
+                           "bench_step": f"{SPLIT} split steps + FP64 observables",
+                           "l2": "inputs larger than L2 (psi = 512 MiB)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline,
+                "clocks": res["clocks"],
+                "gpu_launches": res["launches"] * world,
+                "e2e": e2e,
+                "point_updates_per_s": value * N,
+                "observables": [float(x) for x in res["obs"]]}
+        line.update({k: v for k, v in extra.items() if k != "cpu_baseline"})
+        if "cpu_baseline" in extra:
+            line["cpu_baseline"] = extra["cpu_baseline"]
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * ctap.h -- C ABI of libctap, a single-GPU (B300, sm_103a) implementation of
+ * the three-dimensional Fourier split-operator propagation used by
+ * Morgan et al., "Coherent transport by adiabatic passage on atom chips".
+ *
+ * Physics and method (hbar = m = 1):
+ *   i d psi/dt = (-(1/2) Laplacian + V(x,y,z)) psi               (Sec. IV)
+ * advanced by symmetric (Strang) split steps
+ *   psi <- exp(-i V dt/2) F^-1 exp(-i |k|^2 dt/2) F exp(-i V dt/2) psi
+ * (the paper's "Fourier transforms followed by complex multiplications per
+ * time step", Sec. IV), and its imaginary-time variant (dt -> -i dtau, real
+ * factors, renormalised every step) that prepares the guided transverse
+ * ground state used as the initial state (Sec. V).
+ *
+ * Grid and layout conventions (every entry point):
+ *   - psi is complex, interleaved (re, im), C order [nz][ny][nx] (x fastest);
+ *     complex64 (float2) for CTAP_C64 plans, complex128 (double2) for
+ *     CTAP_C128 plans.  psi is caller-owned DEVICE memory (e.g. a torch
+ *     tensor), 16-byte aligned (32-byte for CTAP_C128).
+ *   - box = {xmin, xmax, ymin, ymax, zmin, zmax}; grid point i of an axis with
+ *     n points is lo + i (hi - lo)/n (periodic, hi excluded).
+ *   - wavenumbers k = 2 pi m/(hi - lo), m in FFT order.
+ *   - potentials given to the library are HOST arrays of FP64 and are copied;
+ *     the caller keeps ownership.
+ *
+ * Sizes: every axis a power of two; nx, ny in [8, 1024], nz in [1, 1024];
+ * the xy-plane is split into at most ny row classes so that one class fits in
+ * a CTA's shared memory, and a z-line tile must hold all classes; shapes
+ * outside that envelope return CTAP_ERR_UNSUPPORTED_SIZE (every shape with
+ * nx*ny <= 65536 and nz <= 1024 is inside it).
+ *
+ * Errors: every call returns a ctap_status; no C++ exception crosses the ABI.
+ * A plan is not thread-safe.  ctap_step is asynchronous on the plan's stream;
+ * ctap_observables, ctap_adjoint, ctap_get_potential and ctap_sync
+ * synchronise (with a host-side timeout, see ctap_set_timeout).
+ */
+#ifndef CTAP_H
+#define CTAP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctap_plan *ctap_plan_t;          /* opaque, library-owned */
+
+typedef enum { CTAP_C64 = 0, CTAP_C128 = 1 } ctap_dtype;
+typedef enum { CTAP_REAL = 0, CTAP_IMAG = 1 } ctap_time;
+
+typedef enum {
+    CTAP_OK = 0,
+    CTAP_ERR_INVALID_ARG = 1,       /* null pointer, bad enum, nsteps < 0 ... */
+    CTAP_ERR_UNSUPPORTED_SIZE = 2,  /* grid outside the supported envelope    */
+    CTAP_ERR_DTYPE = 3,             /* dtype mismatch                         */
+    CTAP_ERR_NO_POTENTIAL = 4,      /* step/observables before set_potential  */
+    CTAP_ERR_OOM = 5,               /* device allocation failed               */
+    CTAP_ERR_CUDA = 6,              /* CUDA runtime error (see ctap_last_error)*/
+    CTAP_ERR_TIMEOUT = 7,           /* host-side wait exceeded the timeout    */
+    CTAP_ERR_NONFINITE = 8          /* a reduction produced NaN or Inf        */
+} ctap_status;
+
+/* Create a plan for an nx x ny x nz grid over `box` (6 doubles, host).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream); every launch
+ * of the plan goes to it.  Builds the FP64-generated twiddle tables on the
+ * host and uploads them.  *out receives the plan (NULL on error). */
+ctap_status ctap_plan_create(int nx, int ny, int nz, const double *box,
+                             ctap_dtype dtype, void *cuda_stream, ctap_plan_t *out);
+
+/* Free every device and host resource of the plan (waits for its stream).
+ * Passing NULL returns CTAP_ERR_INVALID_ARG. */
+ctap_status ctap_plan_destroy(ctap_plan_t plan);
+
+/* Potential, general form (Sec. III: any V(x,y,z) on the grid).
+ * V: host FP64 [nz][ny][nx], copied.  Kept on the device in the plan's
+ * precision (FP32 for CTAP_C64, FP64 for CTAP_C128). */
+ctap_status ctap_set_potential(ctap_plan_t plan, const double *V);
+
+/* Potential, additively separable form V = Vx(x) + Vy(y) + Vz(z)
+ * (e.g. the harmonic trap): three host FP64 arrays of nx, ny, nz values.
+ * Phase factors are generated per axis in FP64 on the host. */
+ctap_status ctap_set_potential_separable(ctap_plan_t plan, const double *Vx,
+                                         const double *Vy, const double *Vz);
+
+/* Potential, product form V = g(y) H(x,z): gy host FP64 [ny], Hxz host FP64
+ * [nz][nx]. */
+ctap_status ctap_set_potential_product(ctap_plan_t plan, const double *gy,
+                                       const double *Hxz);
+
+/* Three Gaussian waveguides (the stand-in for the chip guides of Sec. III
+ * and Fig. 1-3): V = -V0 sum_j exp(-((x - x_j(z))^2 + y^2)/(2 s^2)) with
+ * centres x1z[nz], 0, x3z[nz] (host FP64).  Stored in product form.  When
+ * set_regions != 0 the population regions become |x - x_j(z)| < halfwidth
+ * around these centres (otherwise the previous regions are kept: a frozen
+ * mask).  Clears any spline controls. */
+ctap_status ctap_set_guides(ctap_plan_t plan, double V0, double s,
+                            const double *x1z, const double *x3z,
+                            double halfwidth, int set_regions);
+
+/* Same guides with x_1(z) = -d12(z), x_3(z) = +d23(z), where d12 and d23
+ * are natural cubic splines through nknots knots (knots_z ascending, host)
+ * with values c12[m], c23[m].  Required before ctap_adjoint.  nknots in
+ * [2, 64]. */
+ctap_status ctap_set_guides_spline(ctap_plan_t plan, double V0, double s, int nknots,
+                                   const double *knots_z, const double *c12,
+                                   const double *c23, double halfwidth, int set_regions);
+
+/* Copy the potential the plan holds, evaluated in FP64 on the grid, into V
+ * (host, [nz][ny][nx]).  For checking the potential builders. */
+ctap_status ctap_get_potential(ctap_plan_t plan, double *V);
+
+/* Advance psi (device, in place) by nsteps Strang steps of size dt.
+ * mode CTAP_REAL: exp(-i V dt/2), exp(-i |k|^2 dt/2); CTAP_IMAG: real
+ * factors exp(-V dt/2), exp(-|k|^2 dt/2) and renormalisation to
+ * sum |psi|^2 dV = 1 after every step (Sec. V ground-state preparation).
+ * Asynchronous on the plan stream.  nsteps == 0 is a no-op. */
+ctap_status ctap_step(ctap_plan_t plan, void *psi, int nsteps, double dt, ctap_time mode);
+
+/* FP64-accumulated observables of psi (device, not modified), host out[6]:
+ *   out[0] = sum |psi|^2 dV                    (norm)
+ *   out[1] = <T>, out[2] = <V>                  (normalised expectations)
+ *   out[3..5] = population of guides 1..3: sum over |x - x_j(z)| < halfwidth
+ *               of |psi|^2 dV (Sec. V, Fig. 4); 0 without guide regions.
+ * Synchronises.  Returns CTAP_ERR_NONFINITE if any value is NaN/Inf. */
+ctap_status ctap_observables(ctap_plan_t plan, const void *psi, double *out);
+
+/* Gradient of the final population of guide `guide` (1..3) after nsteps
+ * real-time steps from psi0 (device, not modified) with respect to the
+ * spline controls of ctap_set_guides_spline (not in the paper; the
+ * differentiable form of the Fig. 4 observable).  Reverse conjugate-phase
+ * sweep lambda_n = S(-dt) lambda_{n+1}, lambda_N = M psi_N, with forward
+ * states recomputed from checkpoints taken every K steps.  The population
+ * region and psi0 are held fixed.  Outputs (host): *J, grad[0..m-1] =
+ * dJ/dc12, grad[m..2m-1] = dJ/dc23 (m = nknots).  Synchronises. */
+ctap_status ctap_adjoint(ctap_plan_t plan, const void *psi0, int nsteps, double dt,
+                         int K, int guide, double *J, double *grad);
+
+/* Wait for the plan's stream; CTAP_ERR_TIMEOUT after timeout_ms
+ * (timeout_ms <= 0: the plan's default, see ctap_set_timeout). */
+ctap_status ctap_sync(ctap_plan_t plan, int timeout_ms);
+
+/* Host-side timeout for every synchronising call (default 60000 ms). */
+ctap_status ctap_set_timeout(ctap_plan_t plan, int timeout_ms);
+
+/* Kernel launches the plan has issued so far (for accounting). */
+ctap_status ctap_launch_count(ctap_plan_t plan, long long *count);
+
+/* Per-pass timing with CUDA events on the plan stream.  When enabled, every
+ * launch of ctap_step is bracketed by events; ctap_pass_times writes, per
+ * pass kind (0 prologue/epilogue/xy, 1 z, 2 other), the number of launches
+ * and the summed milliseconds since the last reset (synchronises). */
+ctap_status ctap_set_profiling(ctap_plan_t plan, int enable);
+ctap_status ctap_pass_times(ctap_plan_t plan, long long counts[3], double ms[3]);
+
+/* Pass geometry chosen for the plan: info[0] = P (row classes per plane),
+ * info[1] = rows per XY tile, info[2] = columns per Z tile, info[3] = bytes
+ * of one psi, info[4] = threads per CTA. */
+ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);
+
+const char *ctap_status_string(ctap_status s);
+const char *ctap_last_error(ctap_plan_t plan);   /* plan-local message; "" if none */
+const char *ctap_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTAP_H */

@@ -1,0 +1,436 @@
+// kernels.cu -- XY and Z passes of the split-step propagation (Sec. IV),
+// FP64-accumulated reductions and small helper kernels.
+#include "kernels.cuh"
+
+namespace ctap {
+
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+
+// -------------------------------------------------------------- reductions
+// Block sum of NQ doubles, fixed order (warp shuffles, then warp 0): results
+// are bitwise reproducible run to run.
+template <int NQ> __device__ void block_sum_store(double (&acc)[NQ], double *out)
+{
+    __shared__ double red[kNT / 32][NQ];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double v = (lane < kNT / 32) ? red[lane][q] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) out[q] = v;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kicks
+// psi <- exp(-i V tau) psi (real time) or exp(-V tau) psi (imaginary time)
+template <class T>
+__device__ __forceinline__ void kick_point(Cx<T> &v, const Kick<T> &k, const Geom &g, int x,
+                                           int y, int z, bool full)
+{
+    if (k.form == VF_SEPARABLE) {
+        const Lift<T> *t = full ? k.sep_full : k.sep_half;
+        const Lift<T> a = t[x], b = t[g.nx + y], c = t[g.nx + g.ny + z];
+        if (k.imag) {
+            const T f = a.f * b.f * c.f;
+            v.x *= f;
+            v.y *= f;
+        } else {
+            rot_f<T>(v, a.p, a.u);
+            rot_f<T>(v, b.p, b.u);
+            rot_f<T>(v, c.p, c.u);
+            const T s = a.s * b.s * c.s;
+            v.x *= s;
+            v.y *= s;
+        }
+    } else {
+        const T V = (k.form == VF_DENSE) ? k.Vd[((long long)z * g.ny + y) * g.nx + x]
+                                         : k.g[y] * k.H[(long long)z * g.nx + x];
+        const T th = V * (full ? k.tau_full : k.tau_half);
+        if (k.imag) {
+            const T f = dexp(-th);
+            v.x *= f;
+            v.y *= f;
+        } else {
+            T p, u, s;
+            lift_from_angle(-th, p, u, s);
+            rot_f<T>(v, p, u);
+            v.x *= s;
+            v.y *= s;
+        }
+    }
+}
+
+// --------------------------------------------------------------- XY pass
+template <class T, int MAXV>
+__global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(smraw);
+    const Geom &g = a.g;
+    const int z = blockIdx.x >> g.lgP, r = blockIdx.x & (g.P - 1);
+    const long long pbase = (long long)z * g.plane;
+    const int E = g.Ly << g.lgnx;
+    const int flags = a.flags;
+
+    for (int e = threadIdx.x; e < E; e += kNT) {
+        const int j = e >> g.lgnx, x = e & (g.nx - 1);
+        sm[j * g.pitchXY + x] = a.src[pbase + ((long long)(j * g.P + r) << g.lgnx) + x];
+    }
+    __syncthreads();
+
+    if (flags & XY_RED_OBS) {
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int e = threadIdx.x; e < E; e += kNT) {
+            const int j = e >> g.lgnx, x = e & (g.nx - 1), y = r + j * g.P;
+            const Cx<T> v = sm[j * g.pitchXY + x];
+            const double d = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+            double V = 0.0;
+            if (a.vform_obs == VF_DENSE) V = (double)a.k.Vd[(pbase + ((long long)y << g.lgnx)) + x];
+            else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * a.rd.H64[(long long)z * g.nx + x];
+            else if (a.vform_obs == VF_SEPARABLE)
+                V = a.rd.Vsep[x] + a.rd.Vsep[g.nx + y] + a.rd.Vsep[g.nx + g.ny + z];
+            acc[0] += d;
+            acc[1] += V * d;
+            if (a.rd.xc) {
+                const double xq = g.box[0] + (double)x * g.dx;
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (fabs(xq - a.rd.xc[q * g.nz + z]) < a.rd.hw) acc[2 + q] += d;
+            }
+        }
+        block_sum_store<5>(acc, a.partials + (long long)blockIdx.x * 5);
+        __syncthreads();
+    }
+
+    if (flags & XY_IN_MIXED) {
+        axis_inv<MAXV, kNT, T>(sm, LineMap{g.lgLy, 0, g.pitchXY, 1}, g.lgLy, g.apx, a.tw);
+        axis_inv<MAXV, kNT, T>(sm, LineMap{g.lgnx, 0, 1, g.pitchXY}, g.lgnx, g.apy, a.tw);
+    }
+
+    if (flags & (XY_KICK_HALF | XY_KICK_FULL | XY_KICK_SPLIT)) {
+        double nacc[1] = {0.0};
+        for (int e = threadIdx.x; e < E; e += kNT) {
+            const int j = e >> g.lgnx, x = e & (g.nx - 1), y = r + j * g.P;
+            Cx<T> v = sm[j * g.pitchXY + x];
+            kick_point<T>(v, a.k, g, x, y, z, (flags & XY_KICK_FULL) != 0);
+            if (flags & XY_RED_NORM) nacc[0] += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+            if (flags & XY_STATE_OUT)
+                a.state_out[pbase + ((long long)y << g.lgnx) + x] = v;
+            if (flags & XY_KICK_SPLIT) kick_point<T>(v, a.k, g, x, y, z, false);
+            sm[j * g.pitchXY + x] = v;
+        }
+        if (flags & XY_RED_NORM) block_sum_store<1>(nacc, a.partials + blockIdx.x);
+        __syncthreads();
+    }
+
+    if (flags & XY_OUT_MIXED) {
+        axis_fwd<MAXV, kNT, T>(sm, LineMap{g.lgnx, 0, 1, g.pitchXY}, g.lgnx, g.apy, a.tw);
+        axis_fwd<MAXV, kNT, T>(sm, LineMap{g.lgLy, 0, g.pitchXY, 1}, g.lgLy, g.apx, a.tw);
+    }
+
+    for (int e = threadIdx.x; e < E; e += kNT) {
+        const int j = e >> g.lgnx, x = e & (g.nx - 1);
+        a.dst[pbase + ((long long)(j * g.P + r) << g.lgnx) + x] = sm[j * g.pitchXY + x];
+    }
+}
+
+// ---------------------------------------------------------------- Z pass
+// Load the tile (all z, rows k' P + r, columns b w .. b w + w - 1) and
+// finish the forward y-transform: twiddle exp(-2 pi i r k'/ny), P-point DFT
+// over the row classes r.  Result for ky = k' + Ly k2 goes to tile column
+// k2 w + xo.
+template <class T, int P>
+__device__ __forceinline__ void z_load_cross(const ZArgs<T> &a, Cx<T> *sm, int kp, int b)
+{
+    const Geom &g = a.g;
+    const Lift<T> *W = a.tw + g.cross_off;
+    const int ntask = g.nz << g.lgw;
+    for (int t = threadIdx.x; t < ntask; t += kNT) {
+        const int zz = t >> g.lgw, xo = t & (g.w - 1);
+        const long long base = (long long)zz * g.plane + ((long long)(kp * P) << g.lgnx) +
+                               (b << g.lgw) + xo;
+        Cx<T> v[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r) v[r] = a.src[base + ((long long)r << g.lgnx)];
+#pragma unroll
+        for (int r = 1; r < P; ++r) lift_f<T>(v[r], W[(r * kp) & (g.ny - 1)]);
+        dft_fwd<P, 0, 1, T>(v);
+        sfor<P>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            sm[zz * g.pitchZ + (k2 << g.lgw) + xo] = v[brev(k2, P)];
+        });
+    }
+}
+
+// Exact mirror of z_load_cross, storing the rows back.
+template <class T, int P>
+__device__ __forceinline__ void z_store_cross(const ZArgs<T> &a, const Cx<T> *sm, int kp, int b)
+{
+    const Geom &g = a.g;
+    const Lift<T> *W = a.tw + g.cross_off;
+    const int ntask = g.nz << g.lgw;
+    for (int t = threadIdx.x; t < ntask; t += kNT) {
+        const int zz = t >> g.lgw, xo = t & (g.w - 1);
+        const long long base = (long long)zz * g.plane + ((long long)(kp * P) << g.lgnx) +
+                               (b << g.lgw) + xo;
+        Cx<T> v[P];
+        sfor<P>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            v[brev(k2, P)] = sm[zz * g.pitchZ + (k2 << g.lgw) + xo];
+        });
+        dft_inv<P, 0, 1, T>(v);
+#pragma unroll
+        for (int r = 1; r < P; ++r) lift_b<T>(v[r], W[(r * kp) & (g.ny - 1)]);
+#pragma unroll
+        for (int r = 0; r < P; ++r) a.dst[base + ((long long)r << g.lgnx)] = v[r];
+    }
+}
+
+template <class T, int MAXV>
+__global__ void __launch_bounds__(kNT, 1) z_pass_kernel(const ZArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Cx<T> *sm = reinterpret_cast<Cx<T> *>(smraw);
+    const Geom &g = a.g;
+    const int kp = blockIdx.x >> g.nblk_lg, b = blockIdx.x & ((1 << g.nblk_lg) - 1);
+
+    switch (g.P) {
+    case 1: z_load_cross<T, 1>(a, sm, kp, b); break;
+    case 2: z_load_cross<T, 2>(a, sm, kp, b); break;
+    case 4: z_load_cross<T, 4>(a, sm, kp, b); break;
+    case 8: z_load_cross<T, 8>(a, sm, kp, b); break;
+    default: z_load_cross<T, 16>(a, sm, kp, b); break;
+    }
+    __syncthreads();
+
+    const LineMap lz{g.lgC, 0, 1, g.pitchZ};
+    axis_fwd<MAXV, kNT, T>(sm, lz, g.lgC, g.apz, a.tw);
+
+    const int E = g.nz << g.lgC;
+    if (a.observe) {
+        double acc[1] = {0.0};
+        for (int e = threadIdx.x; e < E; e += kNT) {
+            const int zz = e >> g.lgC, col = e & (g.C - 1);
+            const int kx = (b << g.lgw) + (col & (g.w - 1));
+            const int ky = kp + ((col >> g.lgw) << g.lgLy);
+            const Cx<T> v = sm[zz * g.pitchZ + col];
+            const double d = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+            acc[0] += (a.k2h[kx] + a.k2h[g.nx + ky] + a.k2h[g.nx + g.ny + zz]) * d;
+        }
+        block_sum_store<1>(acc, a.partials + blockIdx.x);
+        return;
+    }
+
+    const T sc = a.inv_n * (a.scale ? (T)(*a.scale) : T(1));
+    for (int e = threadIdx.x; e < E; e += kNT) {
+        const int zz = e >> g.lgC, col = e & (g.C - 1);
+        const int kx = (b << g.lgw) + (col & (g.w - 1));
+        const int ky = kp + ((col >> g.lgw) << g.lgLy);
+        const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky], az = a.kin[g.nx + g.ny + zz];
+        Cx<T> v = sm[zz * g.pitchZ + col];
+        if (a.imag) {
+            const T f = ax.f * ay.f * az.f * sc;
+            v.x *= f;
+            v.y *= f;
+        } else {
+            rot_f<T>(v, ax.p, ax.u);
+            rot_f<T>(v, ay.p, ay.u);
+            rot_f<T>(v, az.p, az.u);
+            const T s = ax.s * ay.s * az.s * sc;
+            v.x *= s;
+            v.y *= s;
+        }
+        sm[zz * g.pitchZ + col] = v;
+    }
+    __syncthreads();
+
+    axis_inv<MAXV, kNT, T>(sm, lz, g.lgC, g.apz, a.tw);
+
+    switch (g.P) {
+    case 1: z_store_cross<T, 1>(a, sm, kp, b); break;
+    case 2: z_store_cross<T, 2>(a, sm, kp, b); break;
+    case 4: z_store_cross<T, 4>(a, sm, kp, b); break;
+    case 8: z_store_cross<T, 8>(a, sm, kp, b); break;
+    default: z_store_cross<T, 16>(a, sm, kp, b); break;
+    }
+}
+
+// --------------------------------------------------------------- helpers
+__global__ void reduce_partials_kernel(const double *p, int nblk, int nq, double *out)
+{
+    for (int q = 0; q < nq; ++q) {
+        double acc[1] = {0.0};
+        for (int i = threadIdx.x; i < nblk; i += kNT) acc[0] += p[(long long)i * nq + q];
+        block_sum_store<1>(acc, out + q);
+        __syncthreads();
+    }
+}
+
+__global__ void norm_scale_kernel(const double *p, int nblk, double dV, double *scale)
+{
+    double acc[1] = {0.0};
+    for (int i = threadIdx.x; i < nblk; i += kNT) acc[0] += p[i];
+    __shared__ double tot;
+    block_sum_store<1>(acc, &tot);
+    __syncthreads();
+    if (threadIdx.x == 0) scale[0] = 1.0 / sqrt(tot * dV);
+}
+
+template <class T> __global__ void scale_kernel(Cx<T> *psi, long long n, const double *scale)
+{
+    const T s = (T)scale[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        Cx<T> v = psi[i];
+        v.x *= s;
+        v.y *= s;
+        psi[i] = v;
+    }
+}
+
+template <class T>
+__global__ void mask_kernel(const Cx<T> *psi, Cx<T> *lam, const Geom g, const double *xcj,
+                            double hw, double *partials, long long chunk)
+{
+    const long long n = g.plane * g.nz;
+    const long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    double acc[1] = {0.0};
+    for (long long i = i0 + threadIdx.x; i < i1; i += kNT) {
+        const int x = (int)(i & (g.nx - 1));
+        const int z = (int)(i >> (g.lgnx + g.lgny));
+        const double xq = g.box[0] + (double)x * g.dx;
+        Cx<T> v = psi[i];
+        if (fabs(xq - xcj[z]) < hw) {
+            acc[0] += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        } else {
+            v.x = T(0);
+            v.y = T(0);
+        }
+        lam[i] = v;
+    }
+    block_sum_store<1>(acc, partials + blockIdx.x);
+}
+
+template <class T>
+__global__ void grad_kernel(const Cx<T> *lam, const Cx<T> *psi, const Geom g, const double *g64,
+                            const double *D1, const double *D3, double c, double *R1, double *R3)
+{
+    const int z = blockIdx.x;
+    const long long base = (long long)z * g.plane;
+    double acc[2] = {0.0, 0.0};
+    for (int e = threadIdx.x; e < (int)g.plane; e += kNT) {
+        const int x = e & (g.nx - 1), y = e >> g.lgnx;
+        const Cx<T> l = lam[base + e], p = psi[base + e];
+        const double im = ((double)l.x * (double)p.y - (double)l.y * (double)p.x) * g64[y];
+        acc[0] += im * D1[(long long)z * g.nx + x];
+        acc[1] += im * D3[(long long)z * g.nx + x];
+    }
+    __shared__ double tot[2];
+    block_sum_store<2>(acc, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R1[z] += c * tot[0];
+        R3[z] += c * tot[1];
+    }
+}
+
+// -------------------------------------------------------------- launchers
+int xy_grid(const Geom &g) { return g.nz * g.P; }
+int z_grid(const Geom &g) { return g.Ly << g.nblk_lg; }
+size_t xy_smem(const Geom &g, int esize) { return (size_t)g.Ly * g.pitchXY * esize; }
+size_t z_smem(const Geom &g, int esize) { return (size_t)g.nz * g.pitchZ * esize; }
+int mask_blocks(const Geom &g)
+{
+    const long long n = g.plane * g.nz;
+    long long nb = (n + 8191) / 8192;
+    return (int)(nb < 4096 ? nb : 4096);
+}
+
+template <class T> constexpr int maxv() { return sizeof(T) == 4 ? 32 : 16; }
+
+template <class T> void launch_xy(const XYArgs<T> &a, cudaStream_t st)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(xy_pass_kernel<T, maxv<T>()>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        configured = true;
+    }
+    xy_pass_kernel<T, maxv<T>()><<<xy_grid(a.g), kNT, xy_smem(a.g, sizeof(Cx<T>)), st>>>(a);
+}
+
+template <class T> void launch_z(const ZArgs<T> &a, cudaStream_t st)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(z_pass_kernel<T, maxv<T>()>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        configured = true;
+    }
+    z_pass_kernel<T, maxv<T>()><<<z_grid(a.g), kNT, z_smem(a.g, sizeof(Cx<T>)), st>>>(a);
+}
+
+void launch_reduce(const double *partials, int nblk, int nq, double *out, cudaStream_t st)
+{
+    reduce_partials_kernel<<<1, kNT, 0, st>>>(partials, nblk, nq, out);
+}
+
+void launch_norm_scale(const double *partials, int nblk, double dV, double *scale,
+                       cudaStream_t st)
+{
+    norm_scale_kernel<<<1, kNT, 0, st>>>(partials, nblk, dV, scale);
+}
+
+template <class T> void launch_scale(Cx<T> *psi, long long n, const double *scale, cudaStream_t st)
+{
+    long long nb = (n + kNT - 1) / kNT;
+    scale_kernel<T><<<(int)(nb < 65535 ? nb : 65535), kNT, 0, st>>>(psi, n, scale);
+}
+
+template <class T>
+void launch_mask(const Cx<T> *psi, Cx<T> *lam, const Geom &g, const double *xcj, double hw,
+                 double *partials, int nblk, cudaStream_t st)
+{
+    const long long n = g.plane * g.nz;
+    const long long chunk = (n + nblk - 1) / nblk;
+    mask_kernel<T><<<nblk, kNT, 0, st>>>(psi, lam, g, xcj, hw, partials, chunk);
+}
+
+template <class T>
+void launch_grad(const Cx<T> *lam, const Cx<T> *psi, const Geom &g, const double *g64,
+                 const double *D1, const double *D3, double c, double *R1, double *R3,
+                 cudaStream_t st)
+{
+    grad_kernel<T><<<g.nz, kNT, 0, st>>>(lam, psi, g, g64, D1, D3, c, R1, R3);
+}
+
+template void launch_xy<float>(const XYArgs<float> &, cudaStream_t);
+template void launch_xy<double>(const XYArgs<double> &, cudaStream_t);
+template void launch_z<float>(const ZArgs<float> &, cudaStream_t);
+template void launch_z<double>(const ZArgs<double> &, cudaStream_t);
+template void launch_scale<float>(Cx<float> *, long long, const double *, cudaStream_t);
+template void launch_scale<double>(Cx<double> *, long long, const double *, cudaStream_t);
+template void launch_mask<float>(const Cx<float> *, Cx<float> *, const Geom &, const double *,
+                                 double, double *, int, cudaStream_t);
+template void launch_mask<double>(const Cx<double> *, Cx<double> *, const Geom &, const double *,
+                                  double, double *, int, cudaStream_t);
+template void launch_grad<float>(const Cx<float> *, const Cx<float> *, const Geom &,
+                                 const double *, const double *, const double *, double, double *,
+                                 double *, cudaStream_t);
+template void launch_grad<double>(const Cx<double> *, const Cx<double> *, const Geom &,
+                                  const double *, const double *, const double *, double,
+                                  double *, double *, cudaStream_t);
+
+}  // namespace ctap

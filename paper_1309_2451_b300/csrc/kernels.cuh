@@ -1,0 +1,125 @@
+// kernels.cuh -- argument blocks and launchers of the split-step passes.
+//
+// One Strang step (Sec. IV) is carried by two passes over psi in HBM:
+//
+//   XY pass, one CTA per (z-plane, row class r): the CTA holds the rows
+//     y = r + P j (j < Ly = ny/P) of one plane.  It undoes the previous
+//     step's forward x- and partial y-transforms, applies the potential
+//     factor (both half-kicks merged), and redoes the forward transforms.
+//     The y-transform is split by decimation: an Ly-point DFT over j inside
+//     the CTA and a P-point "cross" DFT over the classes r done by the Z pass,
+//     so no CTA ever needs a whole plane (a 256x256 complex64 plane is 512 KiB,
+//     more than one SM's shared memory).
+//   Z pass, one CTA per (k', block of w kx values): the CTA holds, for every z,
+//     the P rows k' P + r and w columns: it finishes the y-transform (cross
+//     DFT over r), runs the forward z-transform, applies the kinetic factor,
+//     the inverse z-transform and the inverse cross DFT.
+//
+// Between passes psi lives in place, in the mixed representation
+// (kx, k'-partial ky, z); rows keep their position (row j P + r of a plane).
+#pragma once
+
+#include "device_fft.cuh"
+
+namespace ctap {
+
+constexpr int kNT = 512;   // threads per pass CTA
+
+enum VForm { VF_NONE = 0, VF_DENSE = 1, VF_SEPARABLE = 2, VF_PRODUCT = 3 };
+
+enum XYFlags {
+    XY_IN_MIXED = 1,      // input is in the mixed representation: inverse x, y first
+    XY_OUT_MIXED = 2,     // forward y, x before storing
+    XY_KICK_HALF = 4,     // one potential factor with tau = dt/2
+    XY_KICK_FULL = 8,     // one potential factor with tau = dt (two merged halves)
+    XY_KICK_SPLIT = 16,   // two factors of dt/2 with a reduction/state copy between
+    XY_RED_NORM = 32,     // FP64 sum |psi|^2 after the first factor (imaginary time)
+    XY_RED_OBS = 64,      // FP64 observables of the natural-layout input
+    XY_STATE_OUT = 128    // copy the state between the two half factors out
+};
+
+struct Geom {
+    int nx, ny, nz, P, Ly, w, C;
+    int lgnx, lgny, lgnz, lgP, lgLy, lgw, lgC;
+    int pitchXY, pitchZ;
+    int nblk_lg;            // log2(nx / w)
+    long long plane;        // nx * ny
+    double box[6];
+    double dx;
+    AxisPlan apx, apy, apz; // x: length nx; y: length Ly; z: length nz
+    int cross_off;          // offset of the ny-entry table exp(-2 pi i e/ny)
+};
+
+template <class T> struct Kick {
+    int form;
+    int imag;
+    const T *Vd;              // dense, [nz][ny][nx]
+    const T *g;               // product, [ny]
+    const T *H;               // product, [nz][nx]
+    const Lift<T> *sep_half;  // separable, [nx | ny | nz] for tau = dt/2
+    const Lift<T> *sep_full;  // separable, tau = dt
+    T tau_half, tau_full;
+};
+
+// FP64 data for reductions (observables, norms, gradients)
+struct RedData {
+    const double *Vsep;       // [nx | ny | nz] for separable V
+    const double *g64;        // [ny]
+    const double *H64;        // [nz][nx]
+    const double *xc;         // guide centres [3][nz] or null
+    double hw;                // population half-width
+    const double *k2h;        // k^2/2 per axis [nx | ny | nz]
+};
+
+template <class T> struct XYArgs {
+    Geom g;
+    const Lift<T> *tw;
+    Kick<T> k;
+    RedData rd;
+    int vform_obs;            // V form for <V> (VF_*), dense uses k.Vd
+    const Cx<T> *src;
+    Cx<T> *dst;
+    Cx<T> *state_out;         // XY_STATE_OUT target (natural layout) or null
+    double *partials;         // per-CTA reduction results
+    int flags;
+};
+
+template <class T> struct ZArgs {
+    Geom g;
+    const Lift<T> *tw;
+    const Lift<T> *kin;       // [nx | ny | nz] kinetic factors for this dt/mode
+    int imag;
+    T inv_n;                  // 1/N (transforms are unnormalised)
+    const double *scale;      // lazy imaginary-time renormalisation, or null
+    const Cx<T> *src;
+    Cx<T> *dst;
+    const double *k2h;        // for the kinetic-energy reduction
+    double *partials;
+    int observe;              // 1: forward only, reduce sum k^2/2 |psi_k|^2, no store
+};
+
+template <class T> void launch_xy(const XYArgs<T> &a, cudaStream_t st);
+template <class T> void launch_z(const ZArgs<T> &a, cudaStream_t st);
+int xy_grid(const Geom &g);
+int z_grid(const Geom &g);
+size_t xy_smem(const Geom &g, int esize);
+size_t z_smem(const Geom &g, int esize);
+
+// Deterministic fixed-order sum of nblk x nq partials; out[q] (device).
+void launch_reduce(const double *partials, int nblk, int nq, double *out, cudaStream_t st);
+// scale = 1/sqrt(sum partials * dV)  (imaginary-time renormalisation)
+void launch_norm_scale(const double *partials, int nblk, double dV, double *scale,
+                       cudaStream_t st);
+template <class T> void launch_scale(Cx<T> *psi, long long n, const double *scale,
+                                     cudaStream_t st);
+// lambda = M psi on the region |x - xc(z)| < hw; per-CTA sum M |psi|^2.
+template <class T> void launch_mask(const Cx<T> *psi, Cx<T> *lam, const Geom &g,
+                                    const double *xcj, double hw, double *partials,
+                                    int nblk, cudaStream_t st);
+// R_j[z] += c * sum_{x,y} Im(conj(lam) psi) g(y) D_j(z,x), j = 1, 3.
+template <class T> void launch_grad(const Cx<T> *lam, const Cx<T> *psi, const Geom &g,
+                                    const double *g64, const double *D1, const double *D3,
+                                    double c, double *R1, double *R3, cudaStream_t st);
+int mask_blocks(const Geom &g);
+
+}  // namespace ctap

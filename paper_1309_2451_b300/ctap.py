@@ -1,0 +1,263 @@
+"""ctypes binding of libctap (include/ctap.h): argument marshalling only.
+
+Every step of the propagation runs in the library's CUDA kernels; PyTorch
+supplies device memory (psi is a CUDA tensor) and the stream.  There is no
+CPU fallback: without the built library every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libctap.so")
+
+CTAP_C64, CTAP_C128 = 0, 1
+CTAP_REAL, CTAP_IMAG = 0, 1
+STATUS = ["ok", "invalid argument", "unsupported size", "dtype mismatch", "no potential",
+          "out of memory", "CUDA error", "timeout", "non-finite result"]
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class CtapError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        name = STATUS[code] if 0 <= code < len(STATUS) else f"status {code}"
+        super().__init__(f"ctap: {name}" + (f" ({msg})" if msg else ""))
+
+
+def lib():
+    """Load libctap.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libctap.so not built at {LIB_PATH}; run "
+                           "paper_1309_2451_b300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "ctap_plan_create": [i, i, i, _dp, i, _vp, ctypes.POINTER(_vp)],
+        "ctap_plan_destroy": [_vp],
+        "ctap_set_potential": [_vp, _dp],
+        "ctap_set_potential_separable": [_vp, _dp, _dp, _dp],
+        "ctap_set_potential_product": [_vp, _dp, _dp],
+        "ctap_set_guides": [_vp, d, d, _dp, _dp, d, i],
+        "ctap_set_guides_spline": [_vp, d, d, i, _dp, _dp, _dp, d, i],
+        "ctap_get_potential": [_vp, _dp],
+        "ctap_step": [_vp, _vp, i, d, i],
+        "ctap_observables": [_vp, _vp, _dp],
+        "ctap_adjoint": [_vp, _vp, i, d, i, i, _dp, _dp],
+        "ctap_sync": [_vp, i],
+        "ctap_set_timeout": [_vp, i],
+        "ctap_launch_count": [_vp, ctypes.POINTER(ll)],
+        "ctap_set_profiling": [_vp, i],
+        "ctap_pass_times": [_vp, ctypes.POINTER(ll), _dp],
+        "ctap_plan_info": [_vp, ctypes.POINTER(ll)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    for name in ("ctap_status_string", "ctap_version"):
+        getattr(L, name).restype = ctypes.c_char_p
+    L.ctap_status_string.argtypes = [ctypes.c_int]
+    L.ctap_last_error.argtypes = [_vp]
+    L.ctap_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the functions the binding expects the library to export."""
+    return ["ctap_plan_create", "ctap_plan_destroy", "ctap_set_potential",
+            "ctap_set_potential_separable", "ctap_set_potential_product", "ctap_set_guides",
+            "ctap_set_guides_spline", "ctap_get_potential", "ctap_step", "ctap_observables",
+            "ctap_adjoint", "ctap_sync", "ctap_set_timeout", "ctap_launch_count",
+            "ctap_set_profiling", "ctap_pass_times", "ctap_plan_info", "ctap_status_string",
+            "ctap_last_error", "ctap_version"]
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _p(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Plan:
+    """A split-step plan for psi of shape (nz, ny, nx) on `box`.
+
+    dtype "c64" (FP32 bulk, FP64 tables and reductions) or "c128"."""
+
+    def __init__(self, shape, box, dtype="c64", stream=None):
+        import torch
+        self._torch = torch
+        nz, ny, nx = (int(s) for s in shape)
+        self.shape = (nz, ny, nx)
+        self.box = tuple(float(b) for b in box)
+        self.dtype = {"c64": CTAP_C64, "c128": CTAP_C128,
+                      torch.complex64: CTAP_C64, torch.complex128: CTAP_C128}[dtype]
+        self.torch_dtype = torch.complex64 if self.dtype == CTAP_C64 else torch.complex128
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _vp()
+        self._h = None
+        self._check(lib().ctap_plan_create(nx, ny, nz, _p(_f64(self.box, 6)), self.dtype,
+                                           _vp(stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    # ---------------------------------------------------------------- util
+    def _check(self, rc):
+        if rc != 0:
+            msg = ""
+            if getattr(self, "_h", None):
+                msg = lib().ctap_last_error(self._h).decode()
+            raise CtapError(rc, msg)
+
+    def close(self):
+        if self._h:
+            lib().ctap_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _psi(self, psi):
+        t = self._torch
+        if not isinstance(psi, t.Tensor) or not psi.is_cuda:
+            raise TypeError("psi must be a CUDA tensor")
+        if psi.dtype != self.torch_dtype:
+            raise CtapError(3, f"psi is {psi.dtype}, plan is {self.torch_dtype}")
+        if tuple(psi.shape) != self.shape or not psi.is_contiguous():
+            raise ValueError(f"psi must be a contiguous {self.shape} tensor")
+        return _vp(psi.data_ptr())
+
+    # ----------------------------------------------------------- potential
+    def set_potential(self, V):
+        self._check(lib().ctap_set_potential(self._h, _p(_f64(V, int(np.prod(self.shape))))))
+
+    def set_potential_separable(self, Vx, Vy, Vz):
+        nz, ny, nx = self.shape
+        self._check(lib().ctap_set_potential_separable(self._h, _p(_f64(Vx, nx)),
+                                                       _p(_f64(Vy, ny)), _p(_f64(Vz, nz))))
+
+    def set_potential_product(self, gy, Hxz):
+        nz, ny, nx = self.shape
+        self._check(lib().ctap_set_potential_product(self._h, _p(_f64(gy, ny)),
+                                                     _p(_f64(Hxz, nz * nx))))
+
+    def set_guides(self, V0, s, x1z, x3z, halfwidth=1.5, set_regions=True):
+        nz = self.shape[0]
+        self._check(lib().ctap_set_guides(self._h, float(V0), float(s), _p(_f64(x1z, nz)),
+                                          _p(_f64(x3z, nz)), float(halfwidth),
+                                          1 if set_regions else 0))
+
+    def set_guides_spline(self, V0, s, knots, c12, c23, halfwidth=1.5, set_regions=True):
+        k = _f64(knots)
+        self._check(lib().ctap_set_guides_spline(self._h, float(V0), float(s), k.size, _p(k),
+                                                 _p(_f64(c12, k.size)), _p(_f64(c23, k.size)),
+                                                 float(halfwidth), 1 if set_regions else 0))
+        self.nknots = k.size
+
+    def get_potential(self):
+        V = np.empty(self.shape)
+        self._check(lib().ctap_get_potential(self._h, _p(V)))
+        return V
+
+    # ---------------------------------------------------------- propagation
+    def step(self, psi, nsteps, dt, imag=False):
+        self._check(lib().ctap_step(self._h, self._psi(psi), int(nsteps), float(dt),
+                                    CTAP_IMAG if imag else CTAP_REAL))
+        return psi
+
+    def observables(self, psi):
+        out = np.zeros(6)
+        self._check(lib().ctap_observables(self._h, self._psi(psi), _p(out)))
+        return out
+
+    def adjoint(self, psi0, nsteps, dt, K=32, guide=3):
+        m = getattr(self, "nknots", 0)
+        J = np.zeros(1)
+        grad = np.zeros(2 * max(m, 1))
+        self._check(lib().ctap_adjoint(self._h, self._psi(psi0), int(nsteps), float(dt), int(K),
+                                       int(guide), _p(J), _p(grad)))
+        return float(J[0]), grad[:2 * m]
+
+    def sync(self, timeout_ms=0):
+        self._check(lib().ctap_sync(self._h, int(timeout_ms)))
+
+    def set_timeout(self, ms):
+        self._check(lib().ctap_set_timeout(self._h, int(ms)))
+
+    @property
+    def launch_count(self):
+        c = ctypes.c_longlong()
+        self._check(lib().ctap_launch_count(self._h, ctypes.byref(c)))
+        return c.value
+
+    def set_profiling(self, on=True):
+        self._check(lib().ctap_set_profiling(self._h, 1 if on else 0))
+
+    def pass_times(self):
+        counts = (ctypes.c_longlong * 3)()
+        ms = np.zeros(3)
+        self._check(lib().ctap_pass_times(self._h, counts, _p(ms)))
+        return list(counts), ms
+
+    def info(self):
+        out = (ctypes.c_longlong * 5)()
+        self._check(lib().ctap_plan_info(self._h, out))
+        keys = ("row_classes", "rows_per_xy_tile", "cols_per_z_tile", "psi_bytes", "threads")
+        return dict(zip(keys, list(out)))
+
+
+def _adjoint_function():
+    import torch
+
+    class CtapAdjoint(torch.autograd.Function):
+        """J(c12, c23) = final population of one guide after nsteps steps from
+        psi0, for guide separations given by natural-spline controls.  The
+        backward pass returns the adjoint gradient computed by libctap's reverse
+        conjugate-phase sweep (checkpointed every K steps)."""
+
+        @staticmethod
+        def forward(ctx, c12, c23, plan, psi0, nsteps, dt, K, guide, V0, s, knots, halfwidth):
+            plan.set_guides_spline(V0, s, knots, c12.detach().cpu().numpy(),
+                                   c23.detach().cpu().numpy(), halfwidth, set_regions=True)
+            J, grad = plan.adjoint(psi0, nsteps, dt, K, guide)
+            m = len(knots)
+            ctx.save_for_backward(torch.as_tensor(grad[:m], dtype=c12.dtype),
+                                  torch.as_tensor(grad[m:], dtype=c23.dtype))
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            g12, g23 = ctx.saved_tensors
+            return (gJ * g12, gJ * g23) + (None,) * 10
+
+    return CtapAdjoint
+
+
+_CtapAdjoint = None
+
+
+def ctap_adjoint_apply(c12, c23, plan, psi0, nsteps, dt, K=32, guide=3, V0=20.0, s=1.0,
+                       knots=None, halfwidth=1.5):
+    """torch.autograd entry: returns J as a 0-d tensor differentiable in c12, c23."""
+    global _CtapAdjoint
+    if _CtapAdjoint is None:
+        _CtapAdjoint = _adjoint_function()
+    return _CtapAdjoint.apply(c12, c23, plan, psi0, nsteps, dt, K, guide, V0, s, knots,
+                              halfwidth)

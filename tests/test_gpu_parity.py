@@ -1,0 +1,313 @@
+"""GPU parity: libctap (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+* complex128 path: relative L2 <= 1e-12 after 100 steps (and ~1e-13 for a
+  few steps);
+* complex64 path: relative L2 <= 1e-5 after 1000 steps with |norm drift| <
+  1e-6; a few steps stay below 1e-6 (FP32 rounding, ~2^-24 per operation,
+  times the depth of the transforms).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_2451_b300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctap():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_2451_b300 import build, ctap as c
+    build.build()
+    c.lib()
+    return c
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(psi, dtype):
+    t = torch.complex64 if dtype == "c64" else torch.complex128
+    return torch.from_numpy(np.ascontiguousarray(psi)).to(device="cuda", dtype=t)
+
+
+def random_state(shape, seed=0):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    return a / np.linalg.norm(a)
+
+
+def harmonic_plan(ctap, shape, box, dtype, form="separable"):
+    plan = ctap.Plan(shape, box, dtype)
+    vx, vy, vz = wl.harmonic_parts(shape, box)
+    if form == "separable":
+        plan.set_potential_separable(vx, vy, vz)
+    elif form == "dense":
+        plan.set_potential(wl.harmonic_dense(shape, box))
+    return plan, wl.harmonic_dense(shape, box)
+
+
+def guides_plan(ctap, shape, box, dtype):
+    z = wl.axis(shape[0], box[4], box[5])
+    c = wl.guide_centres(z)
+    plan = ctap.Plan(shape, box, dtype)
+    plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    V = oracle.ctap_potential(shape, box, wl.V0, wl.SIGMA_GUIDE, c[0], c[2])
+    return plan, V, c
+
+
+# ------------------------------------------------------------ transforms
+SHAPES = [(8, 8, 8), (1, 8, 8), (1, 16, 64), (32, 16, 8), (64, 32, 16), (16, 8, 128),
+          (2, 128, 128), (4, 128, 256), (2, 256, 256), (128, 8, 8), (1024, 8, 16)]
+
+
+def max_kinetic_phase(shape, box, dt):
+    kmax = [np.pi * n / (box[2 * a + 1] - box[2 * a]) for a, n in enumerate(shape[::-1])]
+    return 0.5 * sum(k * k for k in kmax) * dt
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-13), ("c64", 1e-6)])
+def test_harmonic_steps_match_oracle(ctap, shape, dtype, tol):
+    """Separable potential: covers every row-class split P (1..8), ragged
+    tiles (nz = 1, 8-point axes, 1024-point z-lines) and both precisions.
+
+    White noise fills the whole spectrum, where the kinetic phase k^2 dt/2
+    reaches ~1500 rad on the 1024-point axis; both sides reduce that angle in
+    FP64 with an absolute error ~ eps64 * theta, so the FP64 tolerance grows
+    with theta_max (the FP32 tables are reduced in FP64 before rounding and
+    do not)."""
+    box = (-7.0, 9.0, -8.0, 8.0, -6.5, 6.5)
+    dt, n = 0.05, 3
+    plan, V = harmonic_plan(ctap, shape, box, dtype)
+    psi0 = random_state(shape, 1)
+    psi = to_dev(psi0, dtype)
+    plan.step(psi, n, dt)
+    ref = oracle.step(psi0, V, box, dt, n)
+    if dtype == "c128":
+        tol += 4 * n * 2.2e-16 * max_kinetic_phase(shape, box, dt)
+    assert rel(psi.cpu().numpy(), ref) < tol, plan.info()
+
+
+@pytest.mark.parametrize("form", ["dense", "separable"])
+def test_potential_forms(ctap, form):
+    shape, box = (16, 32, 64), (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
+    plan, V = harmonic_plan(ctap, shape, box, "c128", form)
+    psi0 = wl.coherent_state(shape, box, 2.0)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 20, 0.01)
+    assert rel(psi.cpu().numpy(), oracle.step(psi0, V, box, 0.01, 20)) < 1e-13
+
+
+def test_product_potential(ctap):
+    shape, box = (16, 64, 32), (-6.0, 6.0, -5.0, 5.0, -4.0, 4.0)
+    rng = np.random.default_rng(5)
+    gy = 1.0 + 0.3 * rng.standard_normal(shape[1])
+    H = -3.0 + rng.standard_normal((shape[0], shape[2]))
+    plan = ctap.Plan(shape, box, "c128")
+    plan.set_potential_product(gy, H)
+    V = gy[None, :, None] * H[:, None, :]
+    assert np.array_equal(plan.get_potential(), V)
+    psi0 = random_state(shape, 2)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 10, 0.02)
+    assert rel(psi.cpu().numpy(), oracle.step(psi0, V, box, 0.02, 10)) < 1e-13
+
+
+def test_guides_potential_matches_oracle(ctap):
+    shape, box = (64, 32, 64), wl.CTAP_BOX
+    plan, V, _ = guides_plan(ctap, shape, box, "c128")
+    assert np.max(np.abs(plan.get_potential() - V)) < 1e-12
+
+
+def test_spline_guides_match_oracle_basis(ctap):
+    shape, box = (256, 8, 16), wl.CTAP_BOX
+    c12, c23 = wl.spline_controls()
+    plan = ctap.Plan(shape, box, "c128")
+    plan.set_guides_spline(wl.V0, wl.SIGMA_GUIDE, wl.KNOTS_Z, c12, c23)
+    z = wl.axis(shape[0], box[4], box[5])
+    B = oracle.natural_spline_basis(wl.KNOTS_Z, z)
+    V = oracle.ctap_potential(shape, box, wl.V0, wl.SIGMA_GUIDE, -(c12 @ B), c23 @ B)
+    assert np.max(np.abs(plan.get_potential() - V)) < 1e-11
+
+
+# -------------------------------------------------------- long real time
+def test_ctap_c128_100_steps(ctap):
+    """complex128 guides run: <= 1e-12 relative L2 after 100 steps."""
+    shape, box = (128, 64, 64), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, "c128")
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=4) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 100, 0.005)
+    ref = oracle.step(psi0, V, box, 0.005, 100)
+    assert rel(psi.cpu().numpy(), ref) < 1e-12
+
+
+def test_ctap_c64_1000_steps_accuracy_and_norm(ctap):
+    """complex64 bulk: <= 1e-5 after 1000 steps, norm drift < 1e-6."""
+    shape, box = (64, 32, 32), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=7) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    psi = to_dev(psi0, "c64")
+    n0 = plan.observables(psi)[0]
+    plan.step(psi, 1000, 0.005)
+    ref = oracle.step(psi0, V, box, 0.005, 1000)
+    assert rel(psi.cpu().numpy().astype(complex), ref) < 1e-5
+    assert abs(plan.observables(psi)[0] / n0 - 1.0) < 1e-6
+
+
+# ----------------------------------------------------------- imaginary time
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 2e-6)])
+def test_imaginary_time_guide_ground_state(ctap, dtype, tol):
+    """The transverse prep of the guide workloads: nz = 1 plane with guide 1
+    only, 200 imaginary-time steps at dtau = 0.01, renormalised each step."""
+    shape, box = (1, 128, 128), wl.CTAP_BOX
+    xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
+    plan = ctap.Plan(shape, box, dtype)
+    # guide 1 alone, V = -V0 exp(-y^2/2) exp(-(x - x1)^2/2), in product form
+    y = wl.axis(128, box[2], box[3])
+    x = wl.axis(128, box[0], box[1])
+    gy = np.exp(-y ** 2 / 2)
+    H = -wl.V0 * np.exp(-(x - xc) ** 2 / 2)[None, :]
+    plan.set_potential_product(gy, H)
+    V = gy[None, :, None] * H[:, None, :]
+    psi0 = wl.guide_seed_2d((128, 128), box, xc)
+    psi = to_dev(psi0, dtype)
+    plan.step(psi, 200, 0.01, imag=True)
+    ref = oracle.step(psi0, V, box, 0.01, 200, imag=True)
+    got = psi.cpu().numpy().astype(complex)
+    assert rel(got, ref) < tol
+    assert abs(np.sum(np.abs(got) ** 2) * wl.cell_volume(shape, box) - 1.0) < 10 * tol
+
+
+# --------------------------------------------------------------- observables
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-6)])
+def test_observables_match_oracle(ctap, dtype, tol):
+    shape, box = (64, 64, 32), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, dtype)
+    psi0 = wl.gaussian_sum(shape, (-8, 8, -4, 4, -30, 30), seed=2) \
+        * np.exp(1j * wl.mesh(shape, box)[2])
+    psi = to_dev(psi0, dtype)
+    got = plan.observables(psi)
+    ref = oracle.observables(psi.cpu().numpy().astype(complex), V, box, c, wl.POP_HALFWIDTH)
+    assert np.allclose(got, ref, rtol=tol, atol=tol * 1e-3), (got, ref)
+
+
+def test_observables_separable_and_dense(ctap):
+    shape, box = (32, 16, 32), (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
+    psi0 = wl.coherent_state(shape, box, 1.5)
+    for form in ("separable", "dense"):
+        plan, V = harmonic_plan(ctap, shape, box, "c128", form)
+        got = plan.observables(to_dev(psi0, "c128"))
+        ref = oracle.observables(psi0, V, box)
+        assert np.allclose(got[:3], ref[:3], rtol=1e-12, atol=1e-15)
+        assert np.all(got[3:] == 0.0)
+
+
+# ------------------------------------------------------------------ adjoint
+ADJ_SHAPE = (32, 16, 32)
+ADJ_BOX = (-9.0, 9.0, -6.0, 6.0, -24.0, 24.0)
+ADJ_KNOTS = np.linspace(-24.0, 24.0, 7)
+
+
+def _adjoint_case():
+    c12 = wl.separation(ADJ_KNOTS, wl.ZC_12, dmin=2.0, dmax=4.0, w=8.0)
+    c23 = wl.separation(ADJ_KNOTS, wl.ZC_23, dmin=2.0, dmax=4.0, w=8.0)
+    z = wl.axis(ADJ_SHAPE[0], ADJ_BOX[4], ADJ_BOX[5])
+    x1 = -(c12 @ oracle.natural_spline_basis(ADJ_KNOTS, z))
+    x, y, zz = wl.mesh(ADJ_SHAPE, ADJ_BOX)
+    psi0 = np.exp(-((x - x1[:, None, None]) ** 2 + y ** 2) / 2.0 - (zz + 10.0) ** 2 / 18.0
+                  + 2j * zz)
+    return wl.normalise(psi0.astype(complex), ADJ_BOX), c12, c23
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-9), ("c64", 1e-4)])
+@pytest.mark.parametrize("K", [1, 7, 40])
+def test_adjoint_matches_oracle_gradient(ctap, dtype, tol, K):
+    psi0, c12, c23 = _adjoint_case()
+    dt, n = 0.05, 40
+    J_ref, g_ref = oracle.ctap_gradient(psi0, ADJ_BOX, 20.0, 1.0, ADJ_KNOTS, c12, c23, dt, n, 2)
+    plan = ctap.Plan(ADJ_SHAPE, ADJ_BOX, dtype)
+    plan.set_guides_spline(20.0, 1.0, ADJ_KNOTS, c12, c23, 1.5)
+    J, g = plan.adjoint(to_dev(psi0, dtype), n, dt, K=K, guide=3)
+    assert abs(J - J_ref) < tol * abs(J_ref)
+    scale = np.max(np.abs(g_ref))
+    assert np.max(np.abs(g - g_ref)) < tol * scale, (g, g_ref)
+
+
+def test_adjoint_autograd_function(ctap):
+    psi0, c12, c23 = _adjoint_case()
+    plan = ctap.Plan(ADJ_SHAPE, ADJ_BOX, "c128")
+    t12 = torch.tensor(c12, requires_grad=True)
+    t23 = torch.tensor(c23, requires_grad=True)
+    J = ctap.ctap_adjoint_apply(t12, t23, plan, to_dev(psi0, "c128"), 40, 0.05, K=8, guide=3,
+                                V0=20.0, s=1.0, knots=ADJ_KNOTS)
+    J.backward()
+    _, g_ref = oracle.ctap_gradient(psi0, ADJ_BOX, 20.0, 1.0, ADJ_KNOTS, c12, c23, 0.05, 40, 2)
+    got = np.concatenate([t12.grad.numpy(), t23.grad.numpy()])
+    assert np.max(np.abs(got - g_ref)) < 1e-9 * np.max(np.abs(g_ref))
+
+
+# ------------------------------------------------------------- edge cases
+def test_zero_steps_is_identity_and_runs_are_deterministic(ctap):
+    shape, box = (32, 64, 64), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    psi0 = to_dev(random_state(shape, 3), "c64")
+    a = psi0.clone()
+    plan.step(a, 0, 0.01)
+    assert torch.equal(a, psi0)
+    b = psi0.clone()
+    plan.step(a, 17, 0.01)
+    plan.step(b, 17, 0.01)
+    assert torch.equal(a, b)
+    assert np.array_equal(plan.observables(a), plan.observables(b))
+
+
+def test_errors_are_reported(ctap):
+    shape, box = (8, 8, 8), (-1.0, 1.0, -1.0, 1.0, -1.0, 1.0)
+    plan = ctap.Plan(shape, box, "c64")
+    psi = to_dev(random_state(shape), "c64")
+    with pytest.raises(ctap.CtapError) as e:
+        plan.step(psi, 1, 0.1)
+    assert e.value.code == 4                                   # no potential yet
+    plan.set_potential(np.zeros(shape))
+    with pytest.raises(ctap.CtapError) as e:
+        plan.step(to_dev(random_state(shape), "c128"), 1, 0.1)
+    assert e.value.code == 3                                   # dtype mismatch
+    with pytest.raises(ctap.CtapError) as e:
+        plan.adjoint(psi, 4, 0.1)
+    assert e.value.code == 4                                   # adjoint without spline
+    with pytest.raises(ctap.CtapError) as e:
+        plan.set_potential(np.full(shape, np.nan))
+    assert e.value.code == 1
+    plan.sync(1000)
+
+
+# --------------------------------------------------- full size (bench shape)
+@pytest.mark.slow
+def test_full_size_c64_one_step_and_invariants(ctap):
+    """256x256x1024 complex64 in the launch configuration bench.py times:
+    one step element-wise against the oracle, then norm conservation and
+    time reversibility over 20 steps (properties that hold at any size)."""
+    shape, box = (1024, 256, 256), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=11) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    psi = to_dev(psi0, "c64")
+    plan.step(psi, 1, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, 1)
+    assert rel(psi.cpu().numpy().astype(complex), ref) < 1e-6
+    del ref
+    n0 = plan.observables(psi)[0]
+    start = psi.clone()
+    plan.step(psi, 20, 0.0025)
+    assert abs(plan.observables(psi)[0] / n0 - 1.0) < 1e-6
+    plan.step(psi, 20, -0.0025)
+    assert rel(psi.cpu().numpy().astype(complex), start.cpu().numpy().astype(complex)) < 1e-5
