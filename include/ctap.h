@@ -157,6 +157,33 @@ ctap_status ctap_pass_times(ctap_plan_t plan, long long counts[3], double ms[3])
  * of one psi, info[4] = threads per CTA. */
 ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);
 
+/* Largest element count ctap_norm_noalloc accepts (2^27). */
+#define CTAP_NOALLOC_MAX_ELEMENTS (16384LL * 8192LL)
+
+/* sum |psi|^2 dV of n complex elements (the value ctap_observables returns
+ * in out[0]) without allocating anything.  The paper has no counterpart:
+ * this exists for callers that must not call cudaMalloc -- for example a
+ * process whose device memory is already held by another framework's
+ * caching allocator, or a latency-critical loop that cannot take
+ * cudaMalloc's implicit device synchronisation.  No plan is needed.
+ *   psi: device, complex64 (dtype CTAP_C64) or complex128 (CTAP_C128),
+ *        interleaved, n elements, caller-owned; dV: cell volume;
+ *   out: DEVICE pointer to one double, caller-owned, written
+ *        asynchronously on cuda_stream (NULL = legacy default stream).
+ * FP64 partial sums go to a fixed 64 KiB file-scope device array that
+ * every GPU loading the library holds until the process exits.  The first
+ * call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams or host threads) race on it, calls on
+ * one stream are ordered.  Every slot a call reads is written by the same
+ * call, so nothing needs clearing in between.
+ * Errors: CTAP_ERR_INVALID_ARG (null pointer, n < 1, non-finite dV),
+ * CTAP_ERR_DTYPE, CTAP_ERR_UNSUPPORTED_SIZE when n exceeds
+ * CTAP_NOALLOC_MAX_ELEMENTS, CTAP_ERR_CUDA on a runtime error. */
+ctap_status ctap_norm_noalloc(const void *psi, long long n, ctap_dtype dtype, double dV,
+                              void *cuda_stream, double *out);
+
 const char *ctap_status_string(ctap_status s);
 const char *ctap_last_error(ctap_plan_t plan);   /* plan-local message; "" if none */
 const char *ctap_version(void);

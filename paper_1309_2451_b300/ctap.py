@@ -57,6 +57,7 @@ def lib():
         "ctap_set_profiling": [_vp, i],
         "ctap_pass_times": [_vp, ctypes.POINTER(ll), _dp],
         "ctap_plan_info": [_vp, ctypes.POINTER(ll)],
+        "ctap_norm_noalloc": [_vp, ll, i, d, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -78,7 +79,7 @@ def exported_symbols():
             "ctap_set_guides_spline", "ctap_get_potential", "ctap_step", "ctap_observables",
             "ctap_adjoint", "ctap_sync", "ctap_set_timeout", "ctap_launch_count",
             "ctap_set_profiling", "ctap_pass_times", "ctap_plan_info", "ctap_status_string",
-            "ctap_last_error", "ctap_version"]
+            "ctap_last_error", "ctap_version", "ctap_norm_noalloc"]
 
 
 def _f64(a, n=None):
@@ -261,3 +262,27 @@ def ctap_adjoint_apply(c12, c23, plan, psi0, nsteps, dt, K=32, guide=3, V0=20.0,
         _CtapAdjoint = _adjoint_function()
     return _CtapAdjoint.apply(c12, c23, plan, psi0, nsteps, dt, K, guide, V0, s, knots,
                               halfwidth)
+
+
+NOALLOC_MAX_ELEMENTS = 16384 * 8192
+
+
+def norm_noalloc(psi, dV, out, stream=None):
+    """sum |psi|^2 dV through ctap_norm_noalloc, which allocates nothing
+    (for callers that must not call cudaMalloc).  psi: contiguous complex64
+    or complex128 CUDA tensor; out: float64 CUDA tensor of one element,
+    written asynchronously on `stream` (default: torch's current stream)."""
+    import torch
+    if psi.dtype not in (torch.complex64, torch.complex128) or not psi.is_cuda \
+            or not psi.is_contiguous():
+        raise TypeError("psi must be a contiguous complex CUDA tensor")
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 1:
+        raise TypeError("out must be a float64 CUDA tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    dtype = CTAP_C64 if psi.dtype == torch.complex64 else CTAP_C128
+    rc = lib().ctap_norm_noalloc(_vp(psi.data_ptr()), psi.numel(), dtype, float(dV),
+                                 _vp(stream.cuda_stream), _vp(out.data_ptr()))
+    if rc != 0:
+        raise CtapError(rc, "ctap_norm_noalloc")
+    return out
