@@ -7,10 +7,10 @@
  *   i d psi/dt = (-(1/2) Laplacian + V(x,y,z)) psi               (Sec. IV)
  * advanced by symmetric (Strang) split steps
  *   psi <- exp(-i V dt/2) F^-1 exp(-i |k|^2 dt/2) F exp(-i V dt/2) psi
- * (the paper's "Fourier transforms followed by complex multiplications per
- * time step", Sec. IV), and its imaginary-time variant (dt -> -i dtau, real
- * factors, renormalised every step) that prepares the guided transverse
- * ground state used as the initial state (Sec. V).
+ * (the transforms and pointwise complex products of one step, Sec. IV),
+ * and its imaginary-time variant (dt -> -i dtau, real factors, renormalised
+ * every step) that prepares the guided transverse ground state used as the
+ * initial state (Sec. V).
  *
  * Grid and layout conventions (every entry point):
  *   - psi is complex, interleaved (re, im), C order [nz][ny][nx] (x fastest);

@@ -10,9 +10,9 @@ basis, which is written out here in numpy.
 
 Paper: Morgan, O'Riordan, Crowley, O'Sullivan, Busch, "Coherent transport by
 adiabatic passage on atom chips".  Sec. IV states the method (Fourier split
-operator, FFT-based); Sec. V the initial state (numerical transverse ground
-state of the left guide times a longitudinal Gaussian) and the observable
-(population of each guide versus time, Fig. 4).
+operator, FFT-based); Sec. V the initial state (transverse ground state of
+the left guide, found numerically, times a longitudinal Gaussian) and the
+observable (population of each guide versus time, Fig. 4).
 
 Arrays are numpy complex128 of shape (nz, ny, nx) (x fastest).  ``box`` is
 (xmin, xmax, ymin, ymax, zmin, zmax); grid points are lo + i (hi - lo)/n.
@@ -124,8 +124,8 @@ def step(psi, V, box, dt, nsteps, imag=False):
 
     Sec. IV: Fourier split-operator method.  imag=True is the imaginary-time
     variant (real factors exp(-V dt/2), exp(-k^2 dt/2)) with renormalisation
-    to sum |psi|^2 dV = 1 after every step (Sec. V, ground state "determined
-    numerically")."""
+    to sum |psi|^2 dV = 1 after every step (Sec. V obtains the transverse
+    ground state numerically)."""
     out = _c128(psi).copy()
     nz, ny, nx = out.shape
     Vd = _f64(V)

@@ -14,11 +14,12 @@
  *     psi <- F^-1 exp(-i |k|^2 dt/2) F psi            (kinetic step, k-space)
  *     psi <- exp(-i V dt/2) psi                       (potential half-kick)
  *
- * The paper counts "Fourier transforms and complex multiplications" per step
- * but does not fix the order; the V/2-K-V/2 order is the reading taken here.
+ * The paper states the per-step cost in transforms and pointwise complex
+ * products but does not fix the order; the V/2-K-V/2 order is the reading
+ * taken here.
  * The imaginary-time variant (used to find the transverse ground state,
- * Sec. V, "determined numerically") replaces dt by -i dtau, so every factor
- * becomes real, and renormalises after each step.
+ * which Sec. V obtains numerically without naming the method) replaces dt by
+ * -i dtau, so every factor becomes real, and renormalises after each step.
  *
  * Conventions:
  *   arrays are [nz][ny][nx] with x fastest, complex128 interleaved (re, im);

@@ -1,5 +1,5 @@
 // device_fft.cuh -- shared-memory / register FFT building blocks for the
-// split-step passes (the "Fourier transforms" of the split-operator step,
+// split-step passes (the transforms of the Fourier split-operator step,
 // Sec. IV).  sm_103a, FP32 (complex64) and FP64 (complex128).
 //
 // Every non-trivial twiddle is a rotation applied by three shears
