@@ -10,6 +10,7 @@
 #include <stdexcept>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "plan.hpp"
@@ -217,6 +218,7 @@ template <class T> XYArgs<T> xy_args(PlanState &st, const TabSet *ts, double dt,
     a.rd.k2h = st.d_k2h;
     a.vform_obs = st.vform;
     a.partials = st.d_partials;
+    a.small_angle = (st.vmax * std::fabs(dt) <= 0.5) ? 1 : 0;
     return a;
 }
 
@@ -237,7 +239,10 @@ template <class T> ctap_status go_xy(PlanState &st, const XYArgs<T> &a)
 {
     CTAP_TRY(pre_launch(st));
     int ev = prof_begin(st, 0);
-    launch_xy<T>(a, st.stream);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value)
+        if (st.fast_xy) done = launch_xy_fast(a, st.stream);
+    if (!done) launch_xy<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "xy pass");
 }
@@ -246,7 +251,10 @@ template <class T> ctap_status go_z(PlanState &st, const ZArgs<T> &a)
 {
     CTAP_TRY(pre_launch(st));
     int ev = prof_begin(st, 1);
-    launch_z<T>(a, st.stream);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value)
+        if (st.fast_z) done = launch_z_fast(a, st.stream);
+    if (!done) launch_z<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "z pass");
 }
@@ -478,6 +486,7 @@ void clear_potential(PlanState &st)
     st.h_g.clear();
     st.h_H.clear();
     st.vform = VF_NONE;
+    st.vmax = 0.0;
     invalidate_sep(st);
 }
 
@@ -486,6 +495,10 @@ ctap_status set_product(PlanState &st, const std::vector<double> &gy, const std:
     clear_potential(st);
     st.h_g = gy;
     st.h_H = H;
+    double gm = 0.0, hm = 0.0;
+    for (double v : gy) gm = std::max(gm, std::fabs(v));
+    for (double v : H) hm = std::max(hm, std::fabs(v));
+    st.vmax = gm * hm;
     CTAP_TRY(upload_prec(st, &st.d_g, gy));
     CTAP_TRY(upload_prec(st, &st.d_H, H));
     CTAP_TRY(upload64(st, &st.d_g64, gy));
@@ -599,6 +612,8 @@ ctap_status ctap_plan_create(int nx, int ny, int nz, const double *box, ctap_dty
     st.dV = (box[1] - box[0]) / nx * (box[3] - box[2]) / ny * (box[5] - box[4]) / nz;
     const int maxv = dtype == CTAP_C64 ? 32 : 16;
     const int emax = kNT * maxv;
+    const char *fg = std::getenv("CTAP_FORCE_GENERIC");
+    st.force_generic = fg && fg[0] == '1';
     try {
         build_geometry(st, emax, maxv);
     } catch (const std::exception &) {
@@ -660,6 +675,8 @@ ctap_status ctap_set_potential(ctap_plan_t plan, const double *V)
     for (double v : st->h_V)
         if (!std::isfinite(v)) return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite potential");
     CTAP_TRY(upload_prec(*st, &st->d_Vd, st->h_V));
+    st->vmax = 0.0;
+    for (double v : st->h_V) st->vmax = std::max(st->vmax, std::fabs(v));
     st->vform = VF_DENSE;
     st->have_guides = false;
     st->have_spline = false;
@@ -860,7 +877,7 @@ ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5])
     info[1] = st->geom.Ly;
     info[2] = st->geom.C;
     info[3] = st->N * st->esize;
-    info[4] = kNT;
+    info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0);
     return CTAP_OK;
 }
 

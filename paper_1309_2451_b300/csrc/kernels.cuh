@@ -48,6 +48,8 @@ struct Geom {
     double dx;
     AxisPlan apx, apy, apz; // x: length nx; y: length Ly; z: length nz
     int cross_off;          // offset of the ny-entry table exp(-2 pi i e/ny)
+    int fast_x_off;         // offset of exp(-2 pi i e/nx), e < nx (fast passes)
+    int fast_z_off;         // offset of exp(-2 pi i e/nz), e < nz (fast passes)
 };
 
 template <class T> struct Kick {
@@ -82,6 +84,7 @@ template <class T> struct XYArgs {
     Cx<T> *state_out;         // XY_STATE_OUT target (natural layout) or null
     double *partials;         // per-CTA reduction results
     int flags;
+    int small_angle;          // |V| dt <= 0.5 everywhere: no half-turn reduction
 };
 
 template <class T> struct ZArgs {
@@ -121,5 +124,12 @@ template <class T> void launch_grad(const Cx<T> *lam, const Cx<T> *psi, const Ge
                                     const double *g64, const double *D1, const double *D3,
                                     double c, double *R1, double *R3, cudaStream_t st);
 int mask_blocks(const Geom &g);
+
+// fast_passes.cu: specialised complex64 passes (same layout as the generic
+// ones); the launchers return false when the geometry is not covered.
+bool fast_xy_supported(int nx, int Ly);
+bool fast_z_supported(int nz, int P, int w);
+bool launch_xy_fast(const XYArgs<float> &a, cudaStream_t st);
+bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st);
 
 }  // namespace ctap

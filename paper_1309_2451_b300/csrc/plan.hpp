@@ -36,6 +36,9 @@ struct PlanState {
     double dV;
     Geom geom;
     int timeout_ms = 60000;
+    bool force_generic = false;    // CTAP_FORCE_GENERIC=1 at plan creation
+    bool fast_xy = false, fast_z = false;
+    double vmax = 0.0;             // max |V| over the grid (small-angle kick test)
 
     // FP64-generated tables on the device (Lift<float> or Lift<double>)
     void *d_tw = nullptr;          // Stockham + cross twiddles

@@ -100,6 +100,13 @@ void build_geometry(PlanState &p, int emax, int maxv)
     g.nz = p.nz;
     int P = 1;
     while ((long long)p.nx * p.ny / P > emax) P *= 2;
+    p.fast_xy = false;
+    p.fast_z = false;
+    if (p.dtype == CTAP_C64 && !p.force_generic && p.ny >= 64 && fast_xy_supported(p.nx, 64) &&
+        p.ny / 64 <= 16) {
+        P = p.ny / 64;                       // y-lines of 64 points held in registers
+        p.fast_xy = true;
+    }
     if (P > 16 || P > p.ny) throw std::runtime_error("xy-plane too large for the row-class split");
     int C = emax / p.nz;
     int w = C / P;
@@ -108,6 +115,7 @@ void build_geometry(PlanState &p, int emax, int maxv)
     g.P = P;
     g.Ly = p.ny / P;
     g.w = w;
+    if (p.dtype == CTAP_C64 && !p.force_generic && fast_z_supported(p.nz, P, w)) p.fast_z = true;
     g.C = w * P;
     g.lgnx = lg2(p.nx);
     g.lgny = lg2(p.ny);
@@ -137,6 +145,10 @@ void build_twiddles(PlanState &p, std::vector<unsigned char> &host, int maxv)
     g.apz = make_axis(p.nz, maxv, entries);
     g.cross_off = entries;
     entries += p.ny;
+    g.fast_x_off = entries;
+    entries += p.nx;
+    g.fast_z_off = entries;
+    entries += p.nz;
     host.assign((size_t)entries * lift_size(p), 0);
     const AxisPlan *aps[3] = {&g.apx, &g.apy, &g.apz};
     for (int a = 0; a < 3; ++a) {
@@ -151,10 +163,13 @@ void build_twiddles(PlanState &p, std::vector<unsigned char> &host, int maxv)
             }
         }
     }
-    for (long long e = 0; e < p.ny; ++e) {
-        double pp, u, sg;
-        lift_rational(-2 * e, p.ny, pp, u, sg);              // exp(-2 pi i e/ny)
-        put_any(p, host, (size_t)(g.cross_off + e), pp, u, sg, 1.0);
+    const int full[3][2] = {{g.cross_off, p.ny}, {g.fast_x_off, p.nx}, {g.fast_z_off, p.nz}};
+    for (const auto &f : full) {
+        for (long long e = 0; e < f[1]; ++e) {
+            double pp, u, sg;
+            lift_rational(-2 * e, f[1], pp, u, sg);          // exp(-2 pi i e/n)
+            put_any(p, host, (size_t)(f[0] + e), pp, u, sg, 1.0);
+        }
     }
 }
 

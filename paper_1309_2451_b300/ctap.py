@@ -220,7 +220,7 @@ class Plan:
     def info(self):
         out = (ctypes.c_longlong * 5)()
         self._check(lib().ctap_plan_info(self._h, out))
-        keys = ("row_classes", "rows_per_xy_tile", "cols_per_z_tile", "psi_bytes", "threads")
+        keys = ("row_classes", "rows_per_xy_tile", "cols_per_z_tile", "psi_bytes", "fast_mask")
         return dict(zip(keys, list(out)))
 
 

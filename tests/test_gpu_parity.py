@@ -290,6 +290,67 @@ def test_errors_are_reported(ctap):
     plan.sync(1000)
 
 
+# ------------------------------------------------ specialised complex64 passes
+FAST_SHAPES = [(256, 64, 64), (256, 128, 128), (512, 256, 256), (1024, 64, 256),
+               (256, 256, 256), (8, 128, 256), (64, 64, 64)]
+
+
+@pytest.mark.parametrize("shape", FAST_SHAPES)
+def test_fast_and_generic_passes_match_oracle(ctap, shape, monkeypatch):
+    """The specialised complex64 passes keep the generic passes' layout; both
+    must match the oracle on the same input (guide potential, 3 steps)."""
+    box = wl.CTAP_BOX
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=5) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    assert plan.info()["fast_mask"] & 1, plan.info()
+    psi = to_dev(psi0, "c64")
+    plan.step(psi, 3, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, 3)
+    fast = psi.cpu().numpy().astype(complex)
+    monkeypatch.setenv("CTAP_FORCE_GENERIC", "1")
+    gplan, _, _ = guides_plan(ctap, shape, box, "c64")
+    assert gplan.info()["fast_mask"] == 0
+    psi = to_dev(psi0, "c64")
+    gplan.step(psi, 3, 0.0025)
+    gen = psi.cpu().numpy().astype(complex)
+    assert rel(fast, ref) < 1e-6
+    assert rel(gen, ref) < 1e-6
+    obs_f = plan.observables(to_dev(psi0, "c64"))
+    obs_g = gplan.observables(to_dev(psi0, "c64"))
+    assert np.allclose(obs_f, obs_g, rtol=1e-6, atol=1e-9)
+
+
+def test_fast_passes_long_run(ctap):
+    """300 steps on the specialised passes (fast XY and Z): relative L2
+    < 1e-5 and |norm drift| < 1e-6 against the FP64 oracle."""
+    shape, box = (256, 64, 64), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    assert plan.info()["fast_mask"] == 3
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=8) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    psi = to_dev(psi0, "c64")
+    n0 = plan.observables(psi)[0]
+    plan.step(psi, 300, 0.005)
+    ref = oracle.step(psi0, V, box, 0.005, 300)
+    assert rel(psi.cpu().numpy().astype(complex), ref) < 1e-5
+    assert abs(plan.observables(psi)[0] / n0 - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("imag", [False, True])
+def test_fast_passes_imaginary_time_and_split(ctap, imag):
+    """Imaginary time (split kick + FP64 norm) and the separable potential on
+    the specialised passes."""
+    shape, box = (256, 64, 64), (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
+    plan, V = harmonic_plan(ctap, shape, box, "c64")
+    assert plan.info()["fast_mask"] == 3
+    psi0 = wl.gaussian_sum(shape, box, seed=9)
+    psi = to_dev(psi0, "c64")
+    plan.step(psi, 20, 0.02, imag=imag)
+    ref = oracle.step(psi0, V, box, 0.02, 20, imag=imag)
+    assert rel(psi.cpu().numpy().astype(complex), ref) < 2e-6
+
+
 # --------------------------------------------------- full size (bench shape)
 @pytest.mark.slow
 def test_full_size_c64_one_step_and_invariants(ctap):
