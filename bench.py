@@ -36,7 +36,7 @@ SHAPE = (1024, 256, 256)
 DT = 0.0025
 SPLIT = 50                 # split steps per bench step (one observation interval)
 SPLIT_FP64 = 2
-KERNEL_SOURCES = ["device_fft.cuh", "kernels.cuh", "kernels.cu"]
+KERNEL_SOURCES = ["device_fft.cuh", "kernels.cuh", "kernels.cu", "fast_passes.cu"]
 
 
 def args_():
@@ -216,6 +216,52 @@ def time_e2e(ctap, wl, torch, steps, device, stream, plan):
                 d2h_bytes_per_step=6 * 8)
 
 
+def time_rows(ctap, wl, torch, device, stream):
+    """The hot-path rows outside the headline loop, each timed once with CUDA
+    events: imaginary-time preparation of the guide-1 transverse state
+    (256x256 plane, 200 steps) and the adjoint gradient of the final guide-3
+    population w.r.t. 32 spline controls (128x128x256 complex64, 1000 steps,
+    checkpoints every 32)."""
+    out = {}
+    box = wl.CTAP_BOX
+    xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # a5: imaginary time on the nz = 1 plane
+    prep = ctap.Plan((1, 256, 256), box, "c64", stream=stream)
+    y = wl.axis(256, box[2], box[3])
+    x = wl.axis(256, box[0], box[1])
+    prep.set_potential_product(np.exp(-y ** 2 / 2.0), -wl.V0 * np.exp(-(x - xc) ** 2 / 2.0)[None, :])
+    phi = torch.from_numpy(wl.guide_seed_2d((256, 256), box, xc)).to(device, torch.complex64)
+    with torch.cuda.stream(stream):
+        prep.step(phi.clone(), 10, 0.01, imag=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        prep.step(phi, 200, 0.01, imag=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["imag_prep_256x256"] = {"steps": 200, "ms": ms, "steps_per_s": 200 / (ms * 1e-3)}
+    # a7: adjoint gradient on the adjoint workload
+    shape = (256, 128, 128)
+    plan = ctap.Plan(shape, box, "c64", stream=stream)
+    c12, c23 = wl.spline_controls()
+    plan.set_guides_spline(wl.V0, wl.SIGMA_GUIDE, wl.KNOTS_Z, c12, c23, wl.POP_HALFWIDTH)
+    phi128 = wl.guide_seed_2d((128, 128), box, xc)
+    psi0 = torch.from_numpy(wl.packet_from_transverse(phi128, shape[0], box)).to(device, torch.complex64)
+    with torch.cuda.stream(stream):
+        plan.adjoint(psi0, 64, 0.005, K=32, guide=3)           # warm-up
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        J, grad = plan.adjoint(psi0, 1000, 0.005, K=32, guide=3)
+    el = time.perf_counter() - t0
+    out["adjoint_128x128x256"] = {"steps": 1000, "checkpoint_every": 32, "s": el,
+                                  "forward_equiv_steps_per_s": 1000 / el, "J": J,
+                                  "grad_norm": float(np.linalg.norm(grad))}
+    prep.close()
+    plan.close()
+    return out
+
+
 def cpu_baseline(seconds_cap=30.0):
     """The FP64 oracle, as it stands, on the host cores: split steps of the
     full 256x256x1024 workload, as many as fit in about `seconds_cap`."""
@@ -304,7 +350,9 @@ def run_ours(a):
     hbm, peak_kind = peaks()
     counts, pms = res["counts"], res["pass_ms"]
     kind = 0 if pms[0] >= pms[1] else 1
-    name = "xy_pass_kernel" if kind == 0 else "z_pass_kernel"
+    fast = res["plan"].info()["fast_mask"]
+    name = (("xy_fast_kernel" if fast & 1 else "xy_pass_kernel") if kind == 0
+            else ("z_fast_kernel" if fast & 2 else "z_pass_kernel"))
     avg_ms = pms[kind] / max(counts[kind], 1)
     bytes_launch = 2 * N * esize       # one read and one write of psi
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
@@ -329,6 +377,7 @@ def run_ours(a):
             "dtype": "f64", "obs": [float(x) for x in r64["obs"]]}
         del r64
     if rank == 0 and not a.no_extras:
+        extra["rows"] = time_rows(ctap, wl, torch, device, stream)
         extra["cpu_baseline"] = cpu_baseline()
     e2e = time_e2e(ctap, wl, torch, max(3, a.steps // 4), device, stream, res["plan"])
     if world > 1:

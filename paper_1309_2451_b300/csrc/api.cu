@@ -252,8 +252,10 @@ template <class T> ctap_status go_z(PlanState &st, const ZArgs<T> &a)
     CTAP_TRY(pre_launch(st));
     int ev = prof_begin(st, 1);
     bool done = false;
+    // the fast Z pass moves two columns per 16-byte access
+    const bool aligned = ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15) == 0;
     if constexpr (std::is_same<T, float>::value)
-        if (st.fast_z) done = launch_z_fast(a, st.stream);
+        if (st.fast_z && aligned) done = launch_z_fast(a, st.stream);
     if (!done) launch_z<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "z pass");

@@ -2,43 +2,54 @@
 //
 // Same HBM layout and the same arithmetic definition as the generic passes
 // in kernels.cu (natural kx order, natural k' order, rows j P + r), so plans
-// can mix them; what changes is how the work is kept on chip:
+// can mix them.  What changes is how the work stays on chip.
 //
-// XY pass (NX = RA * RB columns, LY rows, NX threads):
-//   P1  inverse x, last Stockham stage, read straight from HBM (coalesced
-//       rows), rotated back, written to shared memory;
-//   P2  inverse x, first stage (shared -> shared);
-//   P3  one thread per column: the whole LY-point y-line in registers:
-//       inverse y DFT, potential factor, forward y DFT (no shared-memory
-//       round trip between them);
-//   P4  forward x, first stage;  P5 forward x, last stage, written straight
-//       to HBM.
-//   4 shared-memory round trips per point instead of 11.
+// Every middle stage is done IN PLACE per task: a task writes its results
+// back to exactly the shared-memory positions it read, so a stage needs no
+// "load all / barrier / store all" and a task is one small register DFT in a
+// runtime loop (compact code: the fully unrolled alternative stalled on
+// instruction fetch).  For that, real-space x and y are kept inside shared
+// memory in digit-swapped order (position RA (x mod RB) + x div RB for
+// x = RA RB points); HBM always sees natural order.
 //
-// Z pass (NZ = ZA * ZB, tile NZ x (P W), 512 threads):
-//   Z1  read P rows per z from HBM, finish the forward y-transform (cross
-//       twiddle + P-point DFT) in registers, write the tile;
-//   Z2  forward z, first stage;
-//   Z3  forward z last stage, kinetic factor, inverse last stage, all in
-//       registers on the positions the task read;
-//   Z4  inverse z, first stage;  Z5 inverse cross DFT and store to HBM.
-//   The tile is XOR-swizzled (column ^ 4 (z & 3)) so the z-row-major
-//   accesses of Z1/Z5 and the column accesses of Z2-Z4 are conflict-free.
+// XY pass (NX = RA RB columns, LY = YA YB rows of one plane's row class):
+//   P1  inverse x, last Stockham stage, read straight from HBM, rotated back;
+//   P2  inverse x, first stage, in place;
+//   P3a inverse y, last stage (in place);
+//   P3b inverse y first stage -> potential factor -> forward y first stage,
+//       in registers, in place;
+//   P3c forward y, last stage (in place);
+//   P4  forward x, first stage, in place;
+//   P5  forward x, last stage, straight to HBM.
+//
+// Z pass (NZ = ZA ZB, tile NZ x C, C = P W, 256 threads):
+//   Z1  read P rows per z (two columns per thread), finish the forward
+//       y-transform (cross twiddle + P-point DFT), write the tile;
+//   Z2  forward z, first stage, in place;
+//   Z3  forward z last stage, kinetic factor, inverse last stage, in
+//       registers, in place;
+//   Z4  inverse z, first stage, in place;
+//   Z5  inverse cross DFT, store.
+//   Tile columns are XOR-swizzled per z (column ^ W (z mod 16/W)) so that
+//   the z-major accesses of Z1/Z5 and the column accesses of Z2-Z4 are both
+//   free of bank conflicts.
 #include "kernels.cuh"
 
 namespace ctap {
 
 namespace {
 
-// -------------------------------------------------------- small-angle kick
+constexpr int kFastNT = 512;
+
 // exp(-i th) as a lifted rotation for |th| <= 0.5 (no half-turn reduction):
-// p = -tan(-th/2), u = sin(-th) from odd Taylor series (own, |h| <= 0.25).
+// rotation angle a = -th; u = sin(a), p = -tan(a/2) from odd Taylor series
+// (own; |a/2| <= 0.25).
 __device__ __forceinline__ void lift_small(float th, float &p, float &u)
 {
     const float a = -th, a2 = a * a;
     float s = fmadd(a2, 2.75573192e-06f, -1.98412698e-04f);      // 1/9!, -1/7!
-    s = fmadd(a2, s, 8.33333333e-03f);
-    s = fmadd(a2, s, -1.66666667e-01f);
+    s = fmadd(a2, s, 8.33333333e-03f);                           // 1/5!
+    s = fmadd(a2, s, -1.66666667e-01f);                          // -1/3!
     u = fmadd(a2 * a, s, a);
     const float h = 0.5f * a, h2 = h * h;                        // tan h series
     float t = fmadd(h2, 8.86323552e-03f, 2.18694885e-02f);        // 1382/155925, 62/2835
@@ -48,7 +59,6 @@ __device__ __forceinline__ void lift_small(float th, float &p, float &u)
     p = -fmadd(h2 * h, t, h);
 }
 
-template <class T>
 __device__ __forceinline__ void kick_one(float2 &v, float th, int imag, int small)
 {
     if (imag) {
@@ -68,9 +78,58 @@ __device__ __forceinline__ void kick_one(float2 &v, float th, int imag, int smal
     }
 }
 
-template <int NQ> __device__ void block_sum(double (&acc)[NQ], double *out, int nthreads)
+__device__ __forceinline__ void kick_sep(float2 &v, const Lift<float> &a, const Lift<float> &b,
+                                         const Lift<float> &c, int imag)
 {
-    __shared__ double red[32][NQ];
+    if (imag) {
+        const float f = a.f * b.f * c.f;
+        v.x *= f;
+        v.y *= f;
+    } else {
+        rot_f<float>(v, a.p, a.u);
+        rot_f<float>(v, b.p, b.u);
+        rot_f<float>(v, c.p, c.u);
+        const float s = a.s * b.s * c.s;
+        v.x *= s;
+        v.y *= s;
+    }
+}
+
+// R consecutive complex values as R/2 128-bit shared-memory accesses
+// (p must be 16-byte aligned)
+template <int R> __device__ __forceinline__ void load_pairs(const float2 *p, float2 (&v)[R])
+{
+#pragma unroll
+    for (int i = 0; i < R; i += 2) {
+        const float4 w = *reinterpret_cast<const float4 *>(p + i);
+        v[i] = make_float2(w.x, w.y);
+        v[i + 1] = make_float2(w.z, w.w);
+    }
+}
+template <int R> __device__ __forceinline__ void store_pairs(float2 *p, const float2 (&v)[R])
+{
+#pragma unroll
+    for (int i = 0; i < R; i += 2)
+        *reinterpret_cast<float4 *>(p + i) = make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
+}
+// compiler-only fence: keeps table loads from being hoisted en masse (the
+// hoisted loads of a 32-point stage otherwise exceed the register file)
+__device__ __forceinline__ void hoist_fence() { asm volatile("" ::: "memory"); }
+
+__device__ __forceinline__ void ld2(const float2 *p, float2 &a, float2 &b)
+{
+    const float4 w = *reinterpret_cast<const float4 *>(p);
+    a = make_float2(w.x, w.y);
+    b = make_float2(w.z, w.w);
+}
+__device__ __forceinline__ void st2(float2 *p, const float2 &a, const float2 &b)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
+template <int NQ, int NT = kFastNT> __device__ void block_sum(double (&acc)[NQ], double *out)
+{
+    __shared__ double red[NT / 32][NQ];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -83,7 +142,7 @@ template <int NQ> __device__ void block_sum(double (&acc)[NQ], double *out, int 
     if (wid == 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            double v = (lane < nthreads / 32) ? red[lane][q] : 0.0;
+            double v = (lane < NT / 32) ? red[lane][q] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0) out[q] = v;
@@ -94,16 +153,20 @@ template <int NQ> __device__ void block_sum(double (&acc)[NQ], double *out, int 
 }  // namespace
 
 // ======================================================================= XY
-template <int NX, int LY, int RA, int RB, bool IN_MIXED, bool OUT_MIXED>
-__global__ void __launch_bounds__(NX, 1) xy_fast_kernel(const XYArgs<float> a)
+// HOT: the steady real-time step with the product potential (full kick, no
+// reductions, small angles) compiled without per-point flag tests.
+template <int NX, int RA, int RB, int LY, int YA, int YB, bool IN_MIXED, bool OUT_MIXED,
+          bool HOT>
+__global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
 {
-    static_assert(RA * RB == NX, "NX = RA RB");
-    constexpr int NT = NX;
-    constexpr int PITCH = NX + 1;
+    static_assert(RA * RB == NX && YA * YB == LY, "radix split");
+    constexpr int NT = kFastNT;
+    constexpr int PITCH = NX + 2;          // even: rows stay 16-byte aligned
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *sm = reinterpret_cast<float2 *>(smraw);
-    __shared__ float gtab[LY];
-    __shared__ Lift<float> ytab[LY];
+    __shared__ float gtab[LY];              // g(y), y = r + P jy
+    __shared__ float htab[NX];              // H(x, z) tau at swapped position
+    __shared__ Lift<float> ytab[LY];        // separable y factor
 
     const Geom &g = a.g;
     const int t = threadIdx.x;
@@ -111,25 +174,29 @@ __global__ void __launch_bounds__(NX, 1) xy_fast_kernel(const XYArgs<float> a)
     const long long pbase = (long long)z * g.plane;
     const float2 *src = a.src + pbase;
     float2 *dst = a.dst + pbase;
-    const Lift<float> *wx = a.tw + g.fast_x_off;   // exp(-2 pi i e/NX), e < NX
-    const int flags = a.flags;
+    const Lift<float> *wx = a.tw + g.fast_x_off;   // exp(-2 pi i e/NX)
+    const Lift<float> *wy = a.tw + g.fast_y_off;   // exp(-2 pi i e/LY)
+    const int flags = HOT ? XY_KICK_FULL : a.flags;
     const Kick<float> &k = a.k;
     const bool kick = (flags & (XY_KICK_HALF | XY_KICK_FULL | XY_KICK_SPLIT)) != 0;
+    const bool full = (flags & XY_KICK_FULL) != 0;
+    const float tau = full ? k.tau_full : k.tau_half;
 
-    // per-CTA y data of the potential factor
+    auto swx = [](int x) { return RA * (x % RB) + x / RB; };     // natural x -> position
+    auto unswx = [](int p) { return p / RA + RB * (p % RA); };   // position -> natural x
+    auto swy = [](int jy) { return YA * (jy % YB) + jy / YB; };
+
     if (t < LY) {
         const int y = r + t * g.P;
-        if (k.form == VF_PRODUCT) gtab[t] = k.g[y];
-        else if (k.form == VF_SEPARABLE)
-            ytab[t] = ((flags & XY_KICK_FULL) ? k.sep_full : k.sep_half)[g.nx + y];
+        if (HOT || k.form == VF_PRODUCT) gtab[t] = k.g[y];
+        else if (k.form == VF_SEPARABLE) ytab[t] = (full ? k.sep_full : k.sep_half)[g.nx + y];
     }
+    if (t < NX && (HOT || k.form == VF_PRODUCT))
+        htab[t] = k.H[(long long)z * g.nx + unswx(t)] * tau;
 
     if constexpr (IN_MIXED) {
-        // P1: inverse of the last x stage (Ns = RA, radix RB), from HBM
-        constexpr int Q1 = LY * RA / NT;
-#pragma unroll
-        for (int i = 0; i < Q1; ++i) {
-            const int q = t + i * NT;
+        // P1: inverse x, last stage (Ns = RA, radix RB) from HBM
+        for (int q = t; q < LY * RA; q += NT) {
             const int j = q % RA, row = q / RA;
             const float2 *rowp = src + ((long long)(row * g.P + r) << g.lgnx);
             float2 v[RB];
@@ -144,179 +211,197 @@ __global__ void __launch_bounds__(NX, 1) xy_fast_kernel(const XYArgs<float> a)
             for (int rr = 0; rr < RB; ++rr) sm[row * PITCH + j + RA * rr] = v[rr];
         }
         __syncthreads();
-        // P2: inverse of the first x stage (Ns = 1, radix RA)
-        constexpr int Q2 = LY * RB / NT;
-        float2 v2[Q2][RA];
-#pragma unroll
-        for (int i = 0; i < Q2; ++i) {
-            const int q = t + i * NT;
+        // P2: inverse x, first stage (radix RA), in place on block j
+        for (int q = t; q < LY * RB; q += NT) {
             const int row = q % LY, j = q / LY;
-            sfor<RA>([&](auto kc) {
-                constexpr int kk = decltype(kc)::value;
-                v2[i][brev(kk, RA)] = sm[row * PITCH + j * RA + kk];
-            });
+            float2 *bp = sm + row * PITCH + RA * j;
+            float2 v[RA], w[RA];
+            load_pairs<RA>(bp, w);
+#pragma unroll
+            for (int kk = 0; kk < RA; ++kk) v[brev(kk, RA)] = w[kk];
+            dft_inv<RA, 0, 1, float>(v);
+            store_pairs<RA>(bp, v);
         }
         __syncthreads();
+        // P3a: inverse y, last stage (Ns = YA, radix YB), in place; two columns
+        for (int q = t; q < (NX / 2) * YA; q += NT) {
+            const int p = (q % (NX / 2)) * 2, i = q / (NX / 2);
+            float2 v[YB], w[YB];
+            sfor<YB>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                ld2(sm + (i + YA * kk) * PITCH + p, v[brev(kk, YB)], w[brev(kk, YB)]);
+            });
+            dft_inv<YB, 0, 1, float>(v);
+            dft_inv<YB, 0, 1, float>(w);
 #pragma unroll
-        for (int i = 0; i < Q2; ++i) {
-            const int q = t + i * NT;
-            const int row = q % LY, j = q / LY;
-            dft_inv<RA, 0, 1, float>(v2[i]);
+            for (int rr = 1; rr < YB; ++rr) {
+                const Lift<float> tw = wy[i * rr];
+                lift_b<float>(v[rr], tw);
+                lift_b<float>(w[rr], tw);
+            }
 #pragma unroll
-            for (int rr = 0; rr < RA; ++rr) sm[row * PITCH + j + RB * rr] = v2[i][rr];
+            for (int rr = 0; rr < YB; ++rr) st2(sm + (i + YA * rr) * PITCH + p, v[rr], w[rr]);
         }
     } else {
-        // natural rows straight into the tile
+        // natural rows into the swapped tile
         for (int e = t; e < LY * NX; e += NT) {
-            const int row = e / NX, x = e % NX;
-            sm[row * PITCH + x] = src[((long long)(row * g.P + r) << g.lgnx) + x];
+            const int jy = e / NX, x = e % NX;
+            sm[swy(jy) * PITCH + swx(x)] = src[((long long)(jy * g.P + r) << g.lgnx) + x];
         }
     }
     __syncthreads();
 
-    // P3: the y-line of column x = t in registers
+    // P3b: y first stage: inverse -> potential factor -> forward, in registers;
+    // two adjacent column positions per task
     {
-        const int x = t;
-        float2 v[LY];
-        if constexpr (IN_MIXED) {
-            sfor<LY>([&](auto kc) {
-                constexpr int kk = decltype(kc)::value;
-                v[brev(kk, LY)] = sm[kk * PITCH + x];
-            });
-            dft_inv<LY, 0, 1, float>(v);
-        } else {
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int q = t; q < (NX / 2) * YB; q += NT) {
+            const int p0 = (q % (NX / 2)) * 2, i = q / (NX / 2);
+            float2 v[2][YA];
+            if constexpr (IN_MIXED) {
+                sfor<YA>([&](auto kc) {
+                    constexpr int kk = decltype(kc)::value;
+                    ld2(sm + (YA * i + kk) * PITCH + p0, v[0][brev(kk, YA)], v[1][brev(kk, YA)]);
+                });
+                dft_inv<YA, 0, 1, float>(v[0]);
+                dft_inv<YA, 0, 1, float>(v[1]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < LY; ++j) v[j] = sm[j * PITCH + x];
-        }
-        if (flags & XY_RED_OBS) {
-            double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-            const double xq = g.box[0] + (double)x * g.dx;
-            bool in[3] = {false, false, false};
-            if (a.rd.xc)
-                for (int q = 0; q < 3; ++q) in[q] = fabs(xq - a.rd.xc[q * g.nz + z]) < a.rd.hw;
-            const double hz = (a.vform_obs == VF_PRODUCT) ? a.rd.H64[(long long)z * g.nx + x] : 0.0;
-            const double vxz = (a.vform_obs == VF_SEPARABLE)
-                                   ? a.rd.Vsep[x] + a.rd.Vsep[g.nx + g.ny + z] : 0.0;
-#pragma unroll
-            for (int j = 0; j < LY; ++j) {
-                const int y = r + j * g.P;
-                const double d = (double)v[j].x * v[j].x + (double)v[j].y * v[j].y;
-                double V = 0.0;
-                if (a.vform_obs == VF_DENSE) V = (double)k.Vd[pbase + ((long long)y << g.lgnx) + x];
-                else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * hz;
-                else if (a.vform_obs == VF_SEPARABLE) V = vxz + a.rd.Vsep[g.nx + y];
-                acc[0] += d;
-                acc[1] += V * d;
-                acc[2] += in[0] ? d : 0.0;
-                acc[3] += in[1] ? d : 0.0;
-                acc[4] += in[2] ? d : 0.0;
+                for (int rr = 0; rr < YA; ++rr) ld2(sm + (YA * i + rr) * PITCH + p0, v[0][rr], v[1][rr]);
             }
-            block_sum<5>(acc, a.partials + (long long)blockIdx.x * 5, NT);
-        }
-        if (kick) {
-            const bool full = (flags & XY_KICK_FULL) != 0;
-            const float tau = full ? k.tau_full : k.tau_half;
-            double nacc[1] = {0.0};
-            if (k.form == VF_SEPARABLE) {
-                const Lift<float> *tb = full ? k.sep_full : k.sep_half;
-                const Lift<float> lx = tb[x], lz = tb[g.nx + g.ny + z];
-                const Lift<float> *th = k.sep_half;
+            // v[c][rr] is the real-space point jy = i + YB rr, y = r + P jy, x = unswx(p0 + c)
 #pragma unroll
-                for (int j = 0; j < LY; ++j) {
-                    const int y = r + j * g.P;
-                    const Lift<float> ly = ytab[j];
-                    if (k.imag) {
-                        const float f = lx.f * ly.f * lz.f;
-                        v[j].x *= f;
-                        v[j].y *= f;
-                    } else {
-                        rot_f<float>(v[j], lx.p, lx.u);
-                        rot_f<float>(v[j], ly.p, ly.u);
-                        rot_f<float>(v[j], lz.p, lz.u);
-                        const float s = lx.s * ly.s * lz.s;
-                        v[j].x *= s;
-                        v[j].y *= s;
+            for (int c = 0; c < 2; ++c) {
+                const int p = p0 + c, x = unswx(p);
+                if (!HOT && (flags & XY_RED_OBS)) {
+                    const double xq = g.box[0] + (double)x * g.dx;
+                    bool in0 = false, in1 = false, in2 = false;
+                    if (a.rd.xc) {
+                        in0 = fabs(xq - a.rd.xc[z]) < a.rd.hw;
+                        in1 = fabs(xq - a.rd.xc[g.nz + z]) < a.rd.hw;
+                        in2 = fabs(xq - a.rd.xc[2 * g.nz + z]) < a.rd.hw;
                     }
-                    if (flags & XY_RED_NORM)
-                        nacc[0] += (double)v[j].x * v[j].x + (double)v[j].y * v[j].y;
-                    if (flags & XY_STATE_OUT)
-                        a.state_out[pbase + ((long long)y << g.lgnx) + x] = v[j];
-                    if (flags & XY_KICK_SPLIT) {
-                        const Lift<float> hx = th[x], hy = th[g.nx + y], hz2 = th[g.nx + g.ny + z];
-                        if (k.imag) {
-                            const float f = hx.f * hy.f * hz2.f;
-                            v[j].x *= f;
-                            v[j].y *= f;
-                        } else {
-                            rot_f<float>(v[j], hx.p, hx.u);
-                            rot_f<float>(v[j], hy.p, hy.u);
-                            rot_f<float>(v[j], hz2.p, hz2.u);
-                            const float s = hx.s * hy.s * hz2.s;
-                            v[j].x *= s;
-                            v[j].y *= s;
+                    const double hz =
+                        (a.vform_obs == VF_PRODUCT) ? a.rd.H64[(long long)z * g.nx + x] : 0.0;
+                    const double vxz = (a.vform_obs == VF_SEPARABLE)
+                                           ? a.rd.Vsep[x] + a.rd.Vsep[g.nx + g.ny + z] : 0.0;
+#pragma unroll
+                    for (int rr = 0; rr < YA; ++rr) {
+                        const int y = r + (i + YB * rr) * g.P;
+                        const float2 u = v[c][rr];
+                        const double d = (double)u.x * u.x + (double)u.y * u.y;
+                        double V = 0.0;
+                        if (a.vform_obs == VF_DENSE) V = (double)k.Vd[pbase + ((long long)y << g.lgnx) + x];
+                        else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * hz;
+                        else if (a.vform_obs == VF_SEPARABLE) V = vxz + a.rd.Vsep[g.nx + y];
+                        acc[0] += d;
+                        acc[1] += V * d;
+                        acc[2] += in0 ? d : 0.0;
+                        acc[3] += in1 ? d : 0.0;
+                        acc[4] += in2 ? d : 0.0;
+                    }
+                }
+                if (HOT) {
+                    const float hx = htab[p];
+#pragma unroll
+                    for (int rr = 0; rr < YA; ++rr) {
+                        float pp, u;
+                        lift_small(gtab[i + YB * rr] * hx, pp, u);
+                        rot_f<float>(v[c][rr], pp, u);
+                    }
+                } else if (kick) {
+                    if (k.form == VF_SEPARABLE) {
+                        const Lift<float> *tb = full ? k.sep_full : k.sep_half;
+                        const Lift<float> lx = tb[x], lz = tb[g.nx + g.ny + z];
+                        const Lift<float> hx = k.sep_half[x], hz = k.sep_half[g.nx + g.ny + z];
+#pragma unroll
+                        for (int rr = 0; rr < YA; ++rr) {
+                            const int jy = i + YB * rr;
+                            kick_sep(v[c][rr], lx, ytab[jy], lz, k.imag);
+                            if (flags & XY_RED_NORM)
+                                acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
+                            if (flags & XY_STATE_OUT)
+                                a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
+                            if (flags & XY_KICK_SPLIT)
+                                kick_sep(v[c][rr], hx, k.sep_half[g.nx + r + jy * g.P], hz, k.imag);
+                        }
+                    } else {
+                        const int small = a.small_angle;
+                        const float hx = (k.form == VF_PRODUCT) ? htab[p] : 0.f;
+#pragma unroll
+                        for (int rr = 0; rr < YA; ++rr) {
+                            const int jy = i + YB * rr;
+                            const float th =
+                                (k.form == VF_PRODUCT)
+                                    ? gtab[jy] * hx
+                                    : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
+                            kick_one(v[c][rr], th, k.imag, small);
+                            if (flags & XY_RED_NORM)
+                                acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
+                            if (flags & XY_STATE_OUT)
+                                a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
+                            if (flags & XY_KICK_SPLIT) kick_one(v[c][rr], th, k.imag, small);
                         }
                     }
                 }
-            } else {
-                const int small = a.small_angle;
-                const float hx = (k.form == VF_PRODUCT) ? k.H[(long long)z * g.nx + x] * tau : 0.f;
-#pragma unroll
-                for (int j = 0; j < LY; ++j) {
-                    const int y = r + j * g.P;
-                    const float th = (k.form == VF_PRODUCT)
-                                         ? gtab[j] * hx
-                                         : k.Vd[pbase + ((long long)y << g.lgnx) + x] * tau;
-                    kick_one<float>(v[j], th, k.imag, small);
-                    if (flags & XY_RED_NORM)
-                        nacc[0] += (double)v[j].x * v[j].x + (double)v[j].y * v[j].y;
-                    if (flags & XY_STATE_OUT)
-                        a.state_out[pbase + ((long long)y << g.lgnx) + x] = v[j];
-                    if (flags & XY_KICK_SPLIT) kick_one<float>(v[j], th, k.imag, small);
-                }
             }
-            if (flags & XY_RED_NORM) block_sum<1>(nacc, a.partials + blockIdx.x, NT);
-        }
-        if constexpr (OUT_MIXED) {
-            dft_fwd<LY, 0, 1, float>(v);
-            sfor<LY>([&](auto kc) {
-                constexpr int kk = decltype(kc)::value;
-                sm[kk * PITCH + x] = v[brev(kk, LY)];
-            });
-        } else {
+            if constexpr (OUT_MIXED) {
+                dft_fwd<YA, 0, 1, float>(v[0]);
+                dft_fwd<YA, 0, 1, float>(v[1]);
+                sfor<YA>([&](auto kc) {
+                    constexpr int kk = decltype(kc)::value;
+                    st2(sm + (YA * i + kk) * PITCH + p0, v[0][brev(kk, YA)], v[1][brev(kk, YA)]);
+                });
+            } else {
 #pragma unroll
-            for (int j = 0; j < LY; ++j) sm[j * PITCH + x] = v[j];
+                for (int rr = 0; rr < YA; ++rr) st2(sm + (YA * i + rr) * PITCH + p0, v[0][rr], v[1][rr]);
+            }
+        }
+        if (!HOT) {
+            if (flags & XY_RED_OBS) block_sum<5>(acc, a.partials + (long long)blockIdx.x * 5);
+            else if (flags & XY_RED_NORM) {
+                double n1[1] = {acc[0]};
+                block_sum<1>(n1, a.partials + blockIdx.x);
+            }
         }
     }
     __syncthreads();
 
     if constexpr (OUT_MIXED) {
-        // P4: forward x, first stage (Ns = 1, radix RA)
-        constexpr int Q4 = LY * RB / NT;
-        float2 v4[Q4][RA];
+        // P3c: forward y, last stage (Ns = YA, radix YB), in place; two columns
+        for (int q = t; q < (NX / 2) * YA; q += NT) {
+            const int p = (q % (NX / 2)) * 2, i = q / (NX / 2);
+            float2 v[YB], w[YB];
 #pragma unroll
-        for (int i = 0; i < Q4; ++i) {
-            const int q = t + i * NT;
-            const int row = q % LY, j = q / LY;
+            for (int rr = 0; rr < YB; ++rr) ld2(sm + (i + YA * rr) * PITCH + p, v[rr], w[rr]);
 #pragma unroll
-            for (int rr = 0; rr < RA; ++rr) v4[i][rr] = sm[row * PITCH + j + RB * rr];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < Q4; ++i) {
-            const int q = t + i * NT;
-            const int row = q % LY, j = q / LY;
-            dft_fwd<RA, 0, 1, float>(v4[i]);
-            sfor<RA>([&](auto kc) {
+            for (int rr = 1; rr < YB; ++rr) {
+                const Lift<float> tw = wy[i * rr];
+                lift_f<float>(v[rr], tw);
+                lift_f<float>(w[rr], tw);
+            }
+            dft_fwd<YB, 0, 1, float>(v);
+            dft_fwd<YB, 0, 1, float>(w);
+            sfor<YB>([&](auto kc) {
                 constexpr int kk = decltype(kc)::value;
-                sm[row * PITCH + j * RA + kk] = v4[i][brev(kk, RA)];
+                st2(sm + (i + YA * kk) * PITCH + p, v[brev(kk, YB)], w[brev(kk, YB)]);
             });
         }
         __syncthreads();
-        // P5: forward x, last stage (Ns = RA, radix RB), straight to HBM
-        constexpr int Q5 = LY * RA / NT;
+        // P4: forward x, first stage (radix RA), in place on block j
+        for (int q = t; q < LY * RB; q += NT) {
+            const int row = q % LY, j = q / LY;
+            float2 *bp = sm + row * PITCH + RA * j;
+            float2 v[RA], w[RA];
+            load_pairs<RA>(bp, v);
+            dft_fwd<RA, 0, 1, float>(v);
 #pragma unroll
-        for (int i = 0; i < Q5; ++i) {
-            const int q = t + i * NT;
+            for (int kk = 0; kk < RA; ++kk) w[kk] = v[brev(kk, RA)];
+            store_pairs<RA>(bp, w);
+        }
+        __syncthreads();
+        // P5: forward x, last stage (Ns = RA, radix RB), straight to HBM
+        for (int q = t; q < LY * RA; q += NT) {
             const int j = q % RA, row = q / RA;
             float2 v[RB];
 #pragma unroll
@@ -332,29 +417,41 @@ __global__ void __launch_bounds__(NX, 1) xy_fast_kernel(const XYArgs<float> a)
         }
     } else {
         for (int e = t; e < LY * NX; e += NT) {
-            const int row = e / NX, x = e % NX;
-            dst[((long long)(row * g.P + r) << g.lgnx) + x] = sm[row * PITCH + x];
+            const int jy = e / NX, x = e % NX;
+            dst[((long long)(jy * g.P + r) << g.lgnx) + x] = sm[swy(jy) * PITCH + swx(x)];
         }
     }
 }
 
 // ======================================================================== Z
+constexpr int kZNT = 256;   // 255-register budget: the z stages hold 32 points each
+
 template <int NZ, int ZA, int ZB, int P, int W>
-__global__ void __launch_bounds__(512, 1) z_fast_kernel(const ZArgs<float> a)
+__global__ void __launch_bounds__(kZNT, (P * W * NZ * 8 <= 65536) ? 2 : 1)
+    z_fast_kernel(const ZArgs<float> a)
 {
     static_assert(ZA * ZB == NZ, "NZ = ZA ZB");
-    constexpr int NT = 512;
+    constexpr int NT = kZNT;
     constexpr int C = P * W;
-    static_assert(C * NZ == NT * 32, "tile of 32 points per thread");
+    constexpr int V2 = (W >= 2) ? 2 : 1;               // columns per load task
+    static_assert(C >= 8, "tile needs at least 8 columns");
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const Geom &g = a.g;
     const int t = threadIdx.x;
     const int kp = blockIdx.x >> g.nblk_lg, b = blockIdx.x & ((1 << g.nblk_lg) - 1);
+    // C >= 16: rows of 16 complex span all 32 banks; rotate W-column blocks by
+    //          z so the W-lane groups of Z1/Z5 land on distinct banks.
+    // C == 8:  two rows share the 32 banks; rotate column pairs by z/2.
     auto at = [](int zz, int col) {
-        return zz * C + (col ^ (C >= 16 ? ((zz & 3) << 2) : 0));
+        if constexpr (C >= 16) {
+            constexpr int SWM = (W < 16) ? (16 / W - 1) : 0;
+            return zz * C + (col ^ ((zz & SWM) * W));
+        } else {
+            return zz * C + (col ^ (((zz >> 1) & 3) * 2));
+        }
     };
-    const Lift<float> *wz = a.tw + g.fast_z_off;   // exp(-2 pi i e/NZ), e < NZ
+    const Lift<float> *wz = a.tw + g.fast_z_off;   // exp(-2 pi i e/NZ)
     const Lift<float> *wc = a.tw + g.cross_off;    // exp(-2 pi i e/ny)
     const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
 
@@ -362,85 +459,88 @@ __global__ void __launch_bounds__(512, 1) z_fast_kernel(const ZArgs<float> a)
 #pragma unroll
     for (int rr = 1; rr < P; ++rr) cw[rr] = wc[(rr * kp) & (g.ny - 1)];
 
-    // Z1: load P rows per (z, xo), forward cross DFT, write the tile
-    {
-        constexpr int Q = NZ * W / NT;
+    // Z1: load P rows per (z, column pair), forward cross DFT, write the tile
+    for (int q = t; q < NZ * (W / V2); q += NT) {
+        const int xo = (q % (W / V2)) * V2, zz = q / (W / V2);
+        const float2 *p = a.src + (long long)zz * g.plane + colbase + xo;
+        float2 v[V2][P];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int q = t + i * NT;
-            const int xo = q % W, zz = q / W;
-            const float2 *p = a.src + (long long)zz * g.plane + colbase + xo;
-            float2 v[P];
-#pragma unroll
-            for (int rr = 0; rr < P; ++rr) v[rr] = p[(long long)rr << g.lgnx];
-#pragma unroll
-            for (int rr = 1; rr < P; ++rr) lift_f<float>(v[rr], cw[rr]);
-            dft_fwd<P, 0, 1, float>(v);
-            sfor<P>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                sm[at(zz, k2 * W + xo)] = v[brev(k2, P)];
-            });
+        for (int rr = 0; rr < P; ++rr) {
+            if constexpr (V2 == 2) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(p + ((long long)rr << g.lgnx));
+                v[0][rr] = make_float2(w4.x, w4.y);
+                v[1][rr] = make_float2(w4.z, w4.w);
+            } else {
+                v[0][rr] = p[(long long)rr << g.lgnx];
+            }
         }
+#pragma unroll
+        for (int c = 0; c < V2; ++c) {
+#pragma unroll
+            for (int rr = 1; rr < P; ++rr) lift_f<float>(v[c][rr], cw[rr]);
+            dft_fwd<P, 0, 1, float>(v[c]);
+        }
+        sfor<P>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            if constexpr (V2 == 2) {
+                const float2 e0 = v[0][brev(k2, P)], e1 = v[1][brev(k2, P)];
+                *reinterpret_cast<float4 *>(sm + at(zz, k2 * W + xo)) =
+                    make_float4(e0.x, e0.y, e1.x, e1.y);
+            } else {
+                sm[at(zz, k2 * W + xo)] = v[0][brev(k2, P)];
+            }
+        });
     }
     __syncthreads();
 
-    // Z2: forward z, first stage (Ns = 1, radix ZA)
-    {
-        constexpr int Q = C * ZB / NT;   // tasks (col, j < NZ/ZA = ZB)
-        float2 v[Q > 0 ? Q : 1][ZA];
+    // Z2: forward z, first stage (radix ZA) on rows j + ZB r, in place
+    for (int q = t; q < C * ZB; q += NT) {
+        const int col = q % C, j = q / C;
+        float2 v[ZA];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int q = t + i * NT;
-            const int col = q % C, j = q / C;
-#pragma unroll
-            for (int rr = 0; rr < ZA; ++rr) v[i][rr] = sm[at(j + ZB * rr, col)];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int q = t + i * NT;
-            const int col = q % C, j = q / C;
-            dft_fwd<ZA, 0, 1, float>(v[i]);
-            sfor<ZA>([&](auto kc) {
-                constexpr int kk = decltype(kc)::value;
-                sm[at(j * ZA + kk, col)] = v[i][brev(kk, ZA)];
-            });
-        }
+        for (int rr = 0; rr < ZA; ++rr) v[rr] = sm[at(j + ZB * rr, col)];
+        dft_fwd<ZA, 0, 1, float>(v);
+        sfor<ZA>([&](auto kc) {
+            constexpr int kk = decltype(kc)::value;
+            sm[at(j + ZB * kk, col)] = v[brev(kk, ZA)];
+        });
     }
     __syncthreads();
 
-    // Z3: forward last stage, kinetic factor (or energy reduction), inverse
+    // Z3: last stage on the contiguous rows ZB jp + j, kinetic factor, inverse
     {
-        constexpr int Q = C * ZA / NT;   // tasks (col, j < ZA)
         const float sc = a.inv_n * (a.scale ? (float)(*a.scale) : 1.0f);
         double acc[1] = {0.0};
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int q = t + i * NT;
-            const int col = q % C, j = q / C;
+        for (int q = t; q < C * ZA; q += NT) {
+            const int col = q % C, jp = q / C;
             const int kx = b * W + (col % W);
             const int ky = kp + ((col / W) << g.lgLy);
             float2 v[ZB];
 #pragma unroll
-            for (int rr = 0; rr < ZB; ++rr) v[rr] = sm[at(j + ZA * rr, col)];
-#pragma unroll
-            for (int rr = 1; rr < ZB; ++rr) lift_f<float>(v[rr], wz[j * rr]);
+            for (int j = 0; j < ZB; ++j) v[j] = sm[at(ZB * jp + j, col)];
+            sfor<ZB - 1>([&](auto jc) {
+                constexpr int j = decltype(jc)::value + 1;
+                if constexpr (j % 8 == 0) hoist_fence();
+                lift_f<float>(v[j], wz[jp * j]);
+            });
             dft_fwd<ZB, 0, 1, float>(v);
+            // register brev(k2) holds kz = jp + ZA k2
             if (a.observe) {
                 const double kxy = a.k2h[kx] + a.k2h[g.nx + ky];
                 sfor<ZB>([&](auto kc) {
-                    constexpr int kk = decltype(kc)::value;
-                    const float2 u = v[brev(kk, ZB)];
-                    acc[0] += (kxy + a.k2h[g.nx + g.ny + j + ZA * kk]) *
+                    constexpr int k2 = decltype(kc)::value;
+                    const float2 u = v[brev(k2, ZB)];
+                    acc[0] += (kxy + a.k2h[g.nx + g.ny + jp + ZA * k2]) *
                               ((double)u.x * u.x + (double)u.y * u.y);
                 });
                 continue;
             }
             const Lift<float> ax = a.kin[kx], ay = a.kin[g.nx + ky];
             sfor<ZB>([&](auto kc) {
-                constexpr int kk = decltype(kc)::value;
-                float2 &u = v[brev(kk, ZB)];
-                const Lift<float> az = a.kin[g.nx + g.ny + j + ZA * kk];
+                constexpr int k2 = decltype(kc)::value;
+                if constexpr (k2 % 8 == 0) hoist_fence();
+                float2 &u = v[brev(k2, ZB)];
+                const Lift<float> az = a.kin[g.nx + g.ny + jp + ZA * k2];
                 if (a.imag) {
                     const float f = ax.f * ay.f * az.f * sc;
                     u.x *= f;
@@ -455,61 +555,63 @@ __global__ void __launch_bounds__(512, 1) z_fast_kernel(const ZArgs<float> a)
                 }
             });
             dft_inv<ZB, 0, 1, float>(v);
+            sfor<ZB - 1>([&](auto jc) {
+                constexpr int j = decltype(jc)::value + 1;
+                if constexpr (j % 8 == 0) hoist_fence();
+                lift_b<float>(v[j], wz[jp * j]);
+            });
 #pragma unroll
-            for (int rr = 1; rr < ZB; ++rr) lift_b<float>(v[rr], wz[j * rr]);
-#pragma unroll
-            for (int rr = 0; rr < ZB; ++rr) sm[at(j + ZA * rr, col)] = v[rr];
+            for (int j = 0; j < ZB; ++j) sm[at(ZB * jp + j, col)] = v[j];
         }
         if (a.observe) {
-            block_sum<1>(acc, a.partials + blockIdx.x, NT);
+            block_sum<1, kZNT>(acc, a.partials + blockIdx.x);
             return;
         }
     }
     __syncthreads();
 
-    // Z4: inverse z, first stage
-    {
-        constexpr int Q = C * ZB / NT;
-        float2 v[Q > 0 ? Q : 1][ZA];
+    // Z4: inverse z, first stage, in place
+    for (int q = t; q < C * ZB; q += NT) {
+        const int col = q % C, j = q / C;
+        float2 v[ZA];
+        sfor<ZA>([&](auto kc) {
+            constexpr int kk = decltype(kc)::value;
+            v[brev(kk, ZA)] = sm[at(j + ZB * kk, col)];
+        });
+        dft_inv<ZA, 0, 1, float>(v);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int q = t + i * NT;
-            const int col = q % C, j = q / C;
-            sfor<ZA>([&](auto kc) {
-                constexpr int kk = decltype(kc)::value;
-                v[i][brev(kk, ZA)] = sm[at(j * ZA + kk, col)];
-            });
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int q = t + i * NT;
-            const int col = q % C, j = q / C;
-            dft_inv<ZA, 0, 1, float>(v[i]);
-#pragma unroll
-            for (int rr = 0; rr < ZA; ++rr) sm[at(j + ZB * rr, col)] = v[i][rr];
-        }
+        for (int rr = 0; rr < ZA; ++rr) sm[at(j + ZB * rr, col)] = v[rr];
     }
     __syncthreads();
 
     // Z5: inverse cross DFT and store
-    {
-        constexpr int Q = NZ * W / NT;
+    for (int q = t; q < NZ * (W / V2); q += NT) {
+        const int xo = (q % (W / V2)) * V2, zz = q / (W / V2);
+        float2 v[V2][P];
+        sfor<P>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            if constexpr (V2 == 2) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(sm + at(zz, k2 * W + xo));
+                v[0][brev(k2, P)] = make_float2(w4.x, w4.y);
+                v[1][brev(k2, P)] = make_float2(w4.z, w4.w);
+            } else {
+                v[0][brev(k2, P)] = sm[at(zz, k2 * W + xo)];
+            }
+        });
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int q = t + i * NT;
-            const int xo = q % W, zz = q / W;
-            float2 v[P];
-            sfor<P>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                v[brev(k2, P)] = sm[at(zz, k2 * W + xo)];
-            });
-            dft_inv<P, 0, 1, float>(v);
+        for (int c = 0; c < V2; ++c) {
+            dft_inv<P, 0, 1, float>(v[c]);
 #pragma unroll
-            for (int rr = 1; rr < P; ++rr) lift_b<float>(v[rr], cw[rr]);
-            float2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
+            for (int rr = 1; rr < P; ++rr) lift_b<float>(v[c][rr], cw[rr]);
+        }
+        float2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
 #pragma unroll
-            for (int rr = 0; rr < P; ++rr) p[(long long)rr << g.lgnx] = v[rr];
+        for (int rr = 0; rr < P; ++rr) {
+            if constexpr (V2 == 2)
+                *reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)) =
+                    make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y);
+            else
+                p[(long long)rr << g.lgnx] = v[0][rr];
         }
     }
 }
@@ -517,29 +619,37 @@ __global__ void __launch_bounds__(512, 1) z_fast_kernel(const ZArgs<float> a)
 // ================================================================ dispatch
 namespace {
 
-template <int NX, int LY, int RA, int RB>
+template <int NX, int RA, int RB>
 bool try_xy(const XYArgs<float> &a, cudaStream_t st)
 {
+    constexpr int LY = 64, YA = 8, YB = 8;
     if (a.g.nx != NX || a.g.Ly != LY) return false;
     const bool in = (a.flags & XY_IN_MIXED) != 0, out = (a.flags & XY_OUT_MIXED) != 0;
-    const size_t smem = (size_t)LY * (NX + 1) * sizeof(float2);
-    static bool cfg = false;      // one flag for all four variants of this shape
+    const size_t smem = (size_t)LY * (NX + 2) * sizeof(float2);
+    static bool cfg = false;      // one flag for all five variants of this shape
     if (!cfg) {
-        cudaFuncSetAttribute(xy_fast_kernel<NX, LY, RA, RB, true, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(xy_fast_kernel<NX, LY, RA, RB, true, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(xy_fast_kernel<NX, LY, RA, RB, false, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(xy_fast_kernel<NX, LY, RA, RB, false, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int sz = (int)smem;
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, true>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, false>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, false, false>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, true, false>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, false, false>, attr, sz);
         cfg = true;
     }
     const int grid = xy_grid(a.g);
-    if (in && out) xy_fast_kernel<NX, LY, RA, RB, true, true><<<grid, NX, smem, st>>>(a);
-    else if (in) xy_fast_kernel<NX, LY, RA, RB, true, false><<<grid, NX, smem, st>>>(a);
-    else if (out) xy_fast_kernel<NX, LY, RA, RB, false, true><<<grid, NX, smem, st>>>(a);
-    else xy_fast_kernel<NX, LY, RA, RB, false, false><<<grid, NX, smem, st>>>(a);
+    const bool hot = a.flags == (XY_IN_MIXED | XY_OUT_MIXED | XY_KICK_FULL) &&
+                     a.k.form == VF_PRODUCT && !a.k.imag && a.small_angle;
+    if (hot)
+        xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, true><<<grid, kFastNT, smem, st>>>(a);
+    else if (in && out)
+        xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, false><<<grid, kFastNT, smem, st>>>(a);
+    else if (in)
+        xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, false, false><<<grid, kFastNT, smem, st>>>(a);
+    else if (out)
+        xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, true, false><<<grid, kFastNT, smem, st>>>(a);
+    else
+        xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, false, false><<<grid, kFastNT, smem, st>>>(a);
     return true;
 }
 
@@ -554,7 +664,7 @@ bool try_z(const ZArgs<float> &a, cudaStream_t st)
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cfg = true;
     }
-    z_fast_kernel<NZ, ZA, ZB, P, W><<<z_grid(a.g), 512, smem, st>>>(a);
+    z_fast_kernel<NZ, ZA, ZB, P, W><<<z_grid(a.g), kZNT, smem, st>>>(a);
     return true;
 }
 
@@ -562,25 +672,24 @@ bool try_z(const ZArgs<float> &a, cudaStream_t st)
 
 bool fast_xy_supported(int nx, int Ly)
 {
-    return (nx == 256 && Ly == 64) || (nx == 128 && Ly == 64) || (nx == 64 && Ly == 64);
+    return Ly == 64 && (nx == 256 || nx == 128 || nx == 64);
 }
 
 bool fast_z_supported(int nz, int P, int w)
 {
-    return (nz == 1024 && ((P == 4 && w == 4) || (P == 1 && w == 16) || (P == 2 && w == 8))) ||
+    return (nz == 1024 && ((P == 4 && w == 2) || (P == 1 && w == 16) || (P == 2 && w == 8))) ||
            (nz == 512 && ((P == 4 && w == 8) || (P == 2 && w == 16))) ||
            (nz == 256 && ((P == 4 && w == 16) || (P == 2 && w == 32) || (P == 1 && w == 64)));
 }
 
 bool launch_xy_fast(const XYArgs<float> &a, cudaStream_t st)
 {
-    return try_xy<256, 64, 16, 16>(a, st) || try_xy<128, 64, 16, 8>(a, st) ||
-           try_xy<64, 64, 8, 8>(a, st);
+    return try_xy<256, 16, 16>(a, st) || try_xy<128, 16, 8>(a, st) || try_xy<64, 8, 8>(a, st);
 }
 
 bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st)
 {
-    return try_z<1024, 32, 32, 4, 4>(a, st) || try_z<1024, 32, 32, 1, 16>(a, st) ||
+    return try_z<1024, 32, 32, 4, 2>(a, st) || try_z<1024, 32, 32, 1, 16>(a, st) ||
            try_z<1024, 32, 32, 2, 8>(a, st) || try_z<512, 32, 16, 4, 8>(a, st) ||
            try_z<512, 32, 16, 2, 16>(a, st) || try_z<256, 16, 16, 4, 16>(a, st) ||
            try_z<256, 16, 16, 2, 32>(a, st) || try_z<256, 16, 16, 1, 64>(a, st);

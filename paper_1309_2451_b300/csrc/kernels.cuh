@@ -50,6 +50,7 @@ struct Geom {
     int cross_off;          // offset of the ny-entry table exp(-2 pi i e/ny)
     int fast_x_off;         // offset of exp(-2 pi i e/nx), e < nx (fast passes)
     int fast_z_off;         // offset of exp(-2 pi i e/nz), e < nz (fast passes)
+    int fast_y_off;         // offset of exp(-2 pi i e/Ly), e < Ly (fast passes)
 };
 
 template <class T> struct Kick {

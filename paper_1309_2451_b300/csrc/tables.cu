@@ -112,6 +112,8 @@ void build_geometry(PlanState &p, int emax, int maxv)
     int w = C / P;
     if (w < 1) throw std::runtime_error("z-lines too long for the row-class count");
     if (w > p.nx) w = p.nx;
+    // the fast Z pass prefers 64 KB tiles (two CTAs per SM) where it has them
+    if (p.dtype == CTAP_C64 && !p.force_generic && w > 2 && fast_z_supported(p.nz, P, 2)) w = 2;
     g.P = P;
     g.Ly = p.ny / P;
     g.w = w;
@@ -149,6 +151,8 @@ void build_twiddles(PlanState &p, std::vector<unsigned char> &host, int maxv)
     entries += p.nx;
     g.fast_z_off = entries;
     entries += p.nz;
+    g.fast_y_off = entries;
+    entries += g.Ly;
     host.assign((size_t)entries * lift_size(p), 0);
     const AxisPlan *aps[3] = {&g.apx, &g.apy, &g.apz};
     for (int a = 0; a < 3; ++a) {
@@ -163,7 +167,8 @@ void build_twiddles(PlanState &p, std::vector<unsigned char> &host, int maxv)
             }
         }
     }
-    const int full[3][2] = {{g.cross_off, p.ny}, {g.fast_x_off, p.nx}, {g.fast_z_off, p.nz}};
+    const int full[4][2] = {{g.cross_off, p.ny}, {g.fast_x_off, p.nx}, {g.fast_z_off, p.nz},
+                            {g.fast_y_off, g.Ly}};
     for (const auto &f : full) {
         for (long long e = 0; e < f[1]; ++e) {
             double pp, u, sg;
