@@ -240,8 +240,10 @@ template <class T> ctap_status go_xy(PlanState &st, const XYArgs<T> &a)
     CTAP_TRY(pre_launch(st));
     int ev = prof_begin(st, 0);
     bool done = false;
+    // the fast XY pass moves two values per 16-byte access
+    const bool aligned = ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15) == 0;
     if constexpr (std::is_same<T, float>::value)
-        if (st.fast_xy) done = launch_xy_fast(a, st.stream);
+        if (st.fast_xy && aligned) done = launch_xy_fast(a, st.stream);
     if (!done) launch_xy<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "xy pass");

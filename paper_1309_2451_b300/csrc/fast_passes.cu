@@ -22,7 +22,7 @@
 //   P4  forward x, first stage, in place;
 //   P5  forward x, last stage, straight to HBM.
 //
-// Z pass (NZ = ZA ZB, tile NZ x C, C = P W, 256 threads):
+// Z pass (NZ = ZA ZB, tile NZ x C, C = P W, 256 or 512 threads):
 //   Z1  read P rows per z (two columns per thread), finish the forward
 //       y-transform (cross twiddle + P-point DFT), write the tile;
 //   Z2  forward z, first stage, in place;
@@ -195,20 +195,36 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         htab[t] = k.H[(long long)z * g.nx + unswx(t)] * tau;
 
     if constexpr (IN_MIXED) {
-        // P1: inverse x, last stage (Ns = RA, radix RB) from HBM
-        for (int q = t; q < LY * RA; q += NT) {
-            const int j = q % RA, row = q / RA;
-            const float2 *rowp = src + ((long long)(row * g.P + r) << g.lgnx);
-            float2 v[RB];
-            sfor<RB>([&](auto kc) {
-                constexpr int kk = decltype(kc)::value;
-                v[brev(kk, RB)] = rowp[j + RA * kk];
-            });
-            dft_inv<RB, 0, 1, float>(v);
+        // P1: inverse x, last stage (Ns = RA, radix RB) from HBM.  All loads of
+        // the thread's tasks are issued before the first is used.
+        {
+            constexpr int NTASK = LY * RA;
+            constexpr int Q = (NTASK + NT - 1) / NT;
+            float2 v[Q][RB];
 #pragma unroll
-            for (int rr = 1; rr < RB; ++rr) lift_b<float>(v[rr], wx[j * rr]);
+            for (int i = 0; i < Q; ++i) {
+                const int q = t + i * NT;
+                if (NTASK % NT == 0 || q < NTASK) {
+                    const int j = q % RA, row = q / RA;
+                    const float2 *rowp = src + ((long long)(row * g.P + r) << g.lgnx);
+                    sfor<RB>([&](auto kc) {
+                        constexpr int kk = decltype(kc)::value;
+                        v[i][brev(kk, RB)] = rowp[j + RA * kk];
+                    });
+                }
+            }
 #pragma unroll
-            for (int rr = 0; rr < RB; ++rr) sm[row * PITCH + j + RA * rr] = v[rr];
+            for (int i = 0; i < Q; ++i) {
+                const int q = t + i * NT;
+                if (NTASK % NT == 0 || q < NTASK) {
+                    const int j = q % RA, row = q / RA;
+                    dft_inv<RB, 0, 1, float>(v[i]);
+#pragma unroll
+                    for (int rr = 1; rr < RB; ++rr) lift_b<float>(v[i][rr], wx[j * rr]);
+#pragma unroll
+                    for (int rr = 0; rr < RB; ++rr) sm[row * PITCH + j + RA * rr] = v[i][rr];
+                }
+            }
         }
         __syncthreads();
         // P2: inverse x, first stage (radix RA), in place on block j
@@ -424,14 +440,15 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
 }
 
 // ======================================================================== Z
-constexpr int kZNT = 256;   // 255-register budget: the z stages hold 32 points each
+// threads per Z CTA: 1024-point lines hold 32 points per stage task and need
+// the 255-register budget of 256 threads; shorter lines fit 512 threads
+__host__ __device__ constexpr int z_threads(int nz) { return nz >= 1024 ? 256 : 512; }
 
 template <int NZ, int ZA, int ZB, int P, int W>
-__global__ void __launch_bounds__(kZNT, (P * W * NZ * 8 <= 65536) ? 2 : 1)
-    z_fast_kernel(const ZArgs<float> a)
+__global__ void __launch_bounds__(z_threads(NZ)) z_fast_kernel(const ZArgs<float> a)
 {
     static_assert(ZA * ZB == NZ, "NZ = ZA ZB");
-    constexpr int NT = kZNT;
+    constexpr int NT = z_threads(NZ);
     constexpr int C = P * W;
     constexpr int V2 = (W >= 2) ? 2 : 1;               // columns per load task
     static_assert(C >= 8, "tile needs at least 8 columns");
@@ -451,45 +468,69 @@ __global__ void __launch_bounds__(kZNT, (P * W * NZ * 8 <= 65536) ? 2 : 1)
             return zz * C + (col ^ (((zz >> 1) & 3) * 2));
         }
     };
-    const Lift<float> *wz = a.tw + g.fast_z_off;   // exp(-2 pi i e/NZ)
     const Lift<float> *wc = a.tw + g.cross_off;    // exp(-2 pi i e/ny)
     const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
+    // z twiddles exp(-2 pi i e/NZ) and z kinetic factors, staged in shared
+    // memory (L1 would lose them to the streaming tile loads)
+    Lift<float> *wz = reinterpret_cast<Lift<float> *>(sm + NZ * C);
+    Lift<float> *kz = wz + NZ;
+    for (int e = t; e < NZ; e += NT) {
+        wz[e] = a.tw[g.fast_z_off + e];
+        if (!a.observe) kz[e] = a.kin[g.nx + g.ny + e];
+    }
 
     Lift<float> cw[P];
 #pragma unroll
     for (int rr = 1; rr < P; ++rr) cw[rr] = wc[(rr * kp) & (g.ny - 1)];
 
-    // Z1: load P rows per (z, column pair), forward cross DFT, write the tile
-    for (int q = t; q < NZ * (W / V2); q += NT) {
-        const int xo = (q % (W / V2)) * V2, zz = q / (W / V2);
-        const float2 *p = a.src + (long long)zz * g.plane + colbase + xo;
-        float2 v[V2][P];
+    // Z1: load P rows per (z, column pair), forward cross DFT, write the tile.
+    // Every load of the thread is issued before any is used (one DRAM latency
+    // per tile instead of one per task).
+    {
+        constexpr int NTASK = NZ * (W / V2);
+        constexpr int Q = (NTASK + NT - 1) / NT;
+        float2 v[Q][V2][P];
 #pragma unroll
-        for (int rr = 0; rr < P; ++rr) {
-            if constexpr (V2 == 2) {
-                const float4 w4 = *reinterpret_cast<const float4 *>(p + ((long long)rr << g.lgnx));
-                v[0][rr] = make_float2(w4.x, w4.y);
-                v[1][rr] = make_float2(w4.z, w4.w);
-            } else {
-                v[0][rr] = p[(long long)rr << g.lgnx];
+        for (int i = 0; i < Q; ++i) {
+            const int q = t + i * NT;
+            if (NTASK % NT == 0 || q < NTASK) {
+                const int xo = (q % (W / V2)) * V2, zz = q / (W / V2);
+                const float2 *p = a.src + (long long)zz * g.plane + colbase + xo;
+#pragma unroll
+                for (int rr = 0; rr < P; ++rr) {
+                    if constexpr (V2 == 2) {
+                        const float4 w4 = __ldcs(reinterpret_cast<const float4 *>(p + ((long long)rr << g.lgnx)));
+                        v[i][0][rr] = make_float2(w4.x, w4.y);
+                        v[i][1][rr] = make_float2(w4.z, w4.w);
+                    } else {
+                        v[i][0][rr] = __ldcs(p + ((long long)rr << g.lgnx));
+                    }
+                }
             }
         }
 #pragma unroll
-        for (int c = 0; c < V2; ++c) {
+        for (int i = 0; i < Q; ++i) {
+            const int q = t + i * NT;
+            if (NTASK % NT == 0 || q < NTASK) {
+                const int xo = (q % (W / V2)) * V2, zz = q / (W / V2);
 #pragma unroll
-            for (int rr = 1; rr < P; ++rr) lift_f<float>(v[c][rr], cw[rr]);
-            dft_fwd<P, 0, 1, float>(v[c]);
-        }
-        sfor<P>([&](auto kc) {
-            constexpr int k2 = decltype(kc)::value;
-            if constexpr (V2 == 2) {
-                const float2 e0 = v[0][brev(k2, P)], e1 = v[1][brev(k2, P)];
-                *reinterpret_cast<float4 *>(sm + at(zz, k2 * W + xo)) =
-                    make_float4(e0.x, e0.y, e1.x, e1.y);
-            } else {
-                sm[at(zz, k2 * W + xo)] = v[0][brev(k2, P)];
+                for (int c = 0; c < V2; ++c) {
+#pragma unroll
+                    for (int rr = 1; rr < P; ++rr) lift_f<float>(v[i][c][rr], cw[rr]);
+                    dft_fwd<P, 0, 1, float>(v[i][c]);
+                }
+                sfor<P>([&](auto kc) {
+                    constexpr int k2 = decltype(kc)::value;
+                    if constexpr (V2 == 2) {
+                        const float2 e0 = v[i][0][brev(k2, P)], e1 = v[i][1][brev(k2, P)];
+                        *reinterpret_cast<float4 *>(sm + at(zz, k2 * W + xo)) =
+                            make_float4(e0.x, e0.y, e1.x, e1.y);
+                    } else {
+                        sm[at(zz, k2 * W + xo)] = v[i][0][brev(k2, P)];
+                    }
+                });
             }
-        });
+        }
     }
     __syncthreads();
 
@@ -540,7 +581,7 @@ __global__ void __launch_bounds__(kZNT, (P * W * NZ * 8 <= 65536) ? 2 : 1)
                 constexpr int k2 = decltype(kc)::value;
                 if constexpr (k2 % 8 == 0) hoist_fence();
                 float2 &u = v[brev(k2, ZB)];
-                const Lift<float> az = a.kin[g.nx + g.ny + jp + ZA * k2];
+                const Lift<float> az = kz[jp + ZA * k2];
                 if (a.imag) {
                     const float f = ax.f * ay.f * az.f * sc;
                     u.x *= f;
@@ -564,7 +605,7 @@ __global__ void __launch_bounds__(kZNT, (P * W * NZ * 8 <= 65536) ? 2 : 1)
             for (int j = 0; j < ZB; ++j) sm[at(ZB * jp + j, col)] = v[j];
         }
         if (a.observe) {
-            block_sum<1, kZNT>(acc, a.partials + blockIdx.x);
+            block_sum<1, NT>(acc, a.partials + blockIdx.x);
             return;
         }
     }
@@ -608,10 +649,10 @@ __global__ void __launch_bounds__(kZNT, (P * W * NZ * 8 <= 65536) ? 2 : 1)
 #pragma unroll
         for (int rr = 0; rr < P; ++rr) {
             if constexpr (V2 == 2)
-                *reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)) =
-                    make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y);
+                __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
+                       make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y));
             else
-                p[(long long)rr << g.lgnx] = v[0][rr];
+                __stcs(p + ((long long)rr << g.lgnx), v[0][rr]);
         }
     }
 }
@@ -657,14 +698,14 @@ template <int NZ, int ZA, int ZB, int P, int W>
 bool try_z(const ZArgs<float> &a, cudaStream_t st)
 {
     if (a.g.nz != NZ || a.g.P != P || a.g.w != W) return false;
-    const size_t smem = (size_t)NZ * P * W * sizeof(float2);
+    const size_t smem = (size_t)NZ * P * W * sizeof(float2) + 2 * NZ * sizeof(Lift<float>);
     static bool cfg = false;
     if (!cfg) {
         cudaFuncSetAttribute(z_fast_kernel<NZ, ZA, ZB, P, W>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cfg = true;
     }
-    z_fast_kernel<NZ, ZA, ZB, P, W><<<z_grid(a.g), kZNT, smem, st>>>(a);
+    z_fast_kernel<NZ, ZA, ZB, P, W><<<z_grid(a.g), z_threads(NZ), smem, st>>>(a);
     return true;
 }
 
@@ -677,7 +718,7 @@ bool fast_xy_supported(int nx, int Ly)
 
 bool fast_z_supported(int nz, int P, int w)
 {
-    return (nz == 1024 && ((P == 4 && w == 2) || (P == 1 && w == 16) || (P == 2 && w == 8))) ||
+    return (nz == 1024 && ((P == 4 && w == 4) || (P == 1 && w == 16) || (P == 2 && w == 8))) ||
            (nz == 512 && ((P == 4 && w == 8) || (P == 2 && w == 16))) ||
            (nz == 256 && ((P == 4 && w == 16) || (P == 2 && w == 32) || (P == 1 && w == 64)));
 }
@@ -689,7 +730,7 @@ bool launch_xy_fast(const XYArgs<float> &a, cudaStream_t st)
 
 bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st)
 {
-    return try_z<1024, 32, 32, 4, 2>(a, st) || try_z<1024, 32, 32, 1, 16>(a, st) ||
+    return try_z<1024, 32, 32, 4, 4>(a, st) || try_z<1024, 32, 32, 1, 16>(a, st) ||
            try_z<1024, 32, 32, 2, 8>(a, st) || try_z<512, 32, 16, 4, 8>(a, st) ||
            try_z<512, 32, 16, 2, 16>(a, st) || try_z<256, 16, 16, 4, 16>(a, st) ||
            try_z<256, 16, 16, 2, 32>(a, st) || try_z<256, 16, 16, 1, 64>(a, st);

@@ -112,8 +112,6 @@ void build_geometry(PlanState &p, int emax, int maxv)
     int w = C / P;
     if (w < 1) throw std::runtime_error("z-lines too long for the row-class count");
     if (w > p.nx) w = p.nx;
-    // the fast Z pass prefers 64 KB tiles (two CTAs per SM) where it has them
-    if (p.dtype == CTAP_C64 && !p.force_generic && w > 2 && fast_z_supported(p.nz, P, 2)) w = 2;
     g.P = P;
     g.Ly = p.ny / P;
     g.w = w;

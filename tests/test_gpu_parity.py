@@ -351,6 +351,22 @@ def test_fast_passes_imaginary_time_and_split(ctap, imag):
     assert rel(psi.cpu().numpy().astype(complex), ref) < 2e-6
 
 
+def test_misaligned_psi_uses_generic_passes(ctap):
+    """A psi view 8 bytes off a 16-byte boundary cannot take the 16-byte
+    vector accesses of the specialised passes; the result must not change."""
+    shape, box = (256, 64, 64), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=12)
+    n = int(np.prod(shape))
+    buf = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+    psi = buf[1:].view(shape)
+    assert psi.data_ptr() % 16 == 8
+    psi.copy_(to_dev(psi0, "c64"))
+    plan.step(psi, 3, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, 3)
+    assert rel(psi.cpu().numpy().astype(complex), ref) < 1e-6
+
+
 # --------------------------------------------------- full size (bench shape)
 @pytest.mark.slow
 def test_full_size_c64_one_step_and_invariants(ctap):
