@@ -174,8 +174,11 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
     const long long pbase = (long long)z * g.plane;
     const float2 *src = a.src + pbase;
     float2 *dst = a.dst + pbase;
-    const Lift<float> *wx = a.tw + g.fast_x_off;   // exp(-2 pi i e/NX)
-    const Lift<float> *wy = a.tw + g.fast_y_off;   // exp(-2 pi i e/LY)
+    // x and y twiddles staged in shared memory (after the tile)
+    Lift<float> *wx = reinterpret_cast<Lift<float> *>(sm + LY * PITCH);   // exp(-2 pi i e/NX)
+    Lift<float> *wy = wx + NX;                                            // exp(-2 pi i e/LY)
+    for (int e = t; e < NX + LY; e += NT)
+        wx[e] = e < NX ? a.tw[g.fast_x_off + e] : a.tw[g.fast_y_off + e - NX];
     const int flags = HOT ? XY_KICK_FULL : a.flags;
     const Kick<float> &k = a.k;
     const bool kick = (flags & (XY_KICK_HALF | XY_KICK_FULL | XY_KICK_SPLIT)) != 0;
@@ -196,7 +199,8 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
 
     if constexpr (IN_MIXED) {
         // P1: inverse x, last stage (Ns = RA, radix RB) from HBM.  All loads of
-        // the thread's tasks are issued before the first is used.
+        // the thread's tasks are issued before the first is used, and before
+        // the barrier that publishes the staged tables (their latencies overlap).
         {
             constexpr int NTASK = LY * RA;
             constexpr int Q = (NTASK + NT - 1) / NT;
@@ -213,6 +217,7 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
                     });
                 }
             }
+            __syncthreads();   // staged tables are read from here on
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int q = t + i * NT;
@@ -259,6 +264,7 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
             for (int rr = 0; rr < YB; ++rr) st2(sm + (i + YA * rr) * PITCH + p, v[rr], w[rr]);
         }
     } else {
+        __syncthreads();   // staged tables are read from here on
         // natural rows into the swapped tile
         for (int e = t; e < LY * NX; e += NT) {
             const int jy = e / NX, x = e % NX;
@@ -445,7 +451,8 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
 __host__ __device__ constexpr int z_threads(int nz) { return nz >= 1024 ? 256 : 512; }
 
 template <int NZ, int ZA, int ZB, int P, int W>
-__global__ void __launch_bounds__(z_threads(NZ)) z_fast_kernel(const ZArgs<float> a)
+__global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
+    z_fast_kernel(const ZArgs<float> a)
 {
     static_assert(ZA * ZB == NZ, "NZ = ZA ZB");
     constexpr int NT = z_threads(NZ);
@@ -459,20 +466,23 @@ __global__ void __launch_bounds__(z_threads(NZ)) z_fast_kernel(const ZArgs<float
     const int kp = blockIdx.x >> g.nblk_lg, b = blockIdx.x & ((1 << g.nblk_lg) - 1);
     // C >= 16: rows of 16 complex span all 32 banks; rotate W-column blocks by
     //          z so the W-lane groups of Z1/Z5 land on distinct banks.
-    // C == 8:  two rows share the 32 banks; rotate column pairs by z/2.
+    // C == 8:  two rows share the 32 banks; rotate column pairs by z/2 (Z1/Z5)
+    //          and shift every other block of 32 rows by half the banks (rows
+    //          z and z + 32 meet in Z3): 8 padding slots after every 32 rows.
     auto at = [](int zz, int col) {
         if constexpr (C >= 16) {
             constexpr int SWM = (W < 16) ? (16 / W - 1) : 0;
             return zz * C + (col ^ ((zz & SWM) * W));
         } else {
-            return zz * C + (col ^ (((zz >> 1) & 3) * 2));
+            return zz * C + (zz >> 5) * 8 + (col ^ (((zz >> 1) & 3) * 2));
         }
     };
     const Lift<float> *wc = a.tw + g.cross_off;    // exp(-2 pi i e/ny)
     const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
     // z twiddles exp(-2 pi i e/NZ) and z kinetic factors, staged in shared
     // memory (L1 would lose them to the streaming tile loads)
-    Lift<float> *wz = reinterpret_cast<Lift<float> *>(sm + NZ * C);
+    constexpr int TILE = NZ * C + (C == 8 ? (NZ / 32) * 8 : 0);   // + row-block padding
+    Lift<float> *wz = reinterpret_cast<Lift<float> *>(sm + TILE);
     Lift<float> *kz = wz + NZ;
     for (int e = t; e < NZ; e += NT) {
         wz[e] = a.tw[g.fast_z_off + e];
@@ -561,7 +571,7 @@ __global__ void __launch_bounds__(z_threads(NZ)) z_fast_kernel(const ZArgs<float
             for (int j = 0; j < ZB; ++j) v[j] = sm[at(ZB * jp + j, col)];
             sfor<ZB - 1>([&](auto jc) {
                 constexpr int j = decltype(jc)::value + 1;
-                if constexpr (j % 8 == 0) hoist_fence();
+                if constexpr (j % 4 == 0) hoist_fence();
                 lift_f<float>(v[j], wz[jp * j]);
             });
             dft_fwd<ZB, 0, 1, float>(v);
@@ -579,7 +589,7 @@ __global__ void __launch_bounds__(z_threads(NZ)) z_fast_kernel(const ZArgs<float
             const Lift<float> ax = a.kin[kx], ay = a.kin[g.nx + ky];
             sfor<ZB>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                if constexpr (k2 % 8 == 0) hoist_fence();
+                if constexpr (k2 % 4 == 0) hoist_fence();
                 float2 &u = v[brev(k2, ZB)];
                 const Lift<float> az = kz[jp + ZA * k2];
                 if (a.imag) {
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(z_threads(NZ)) z_fast_kernel(const ZArgs<float
             dft_inv<ZB, 0, 1, float>(v);
             sfor<ZB - 1>([&](auto jc) {
                 constexpr int j = decltype(jc)::value + 1;
-                if constexpr (j % 8 == 0) hoist_fence();
+                if constexpr (j % 4 == 0) hoist_fence();
                 lift_b<float>(v[j], wz[jp * j]);
             });
 #pragma unroll
@@ -666,7 +676,7 @@ bool try_xy(const XYArgs<float> &a, cudaStream_t st)
     constexpr int LY = 64, YA = 8, YB = 8;
     if (a.g.nx != NX || a.g.Ly != LY) return false;
     const bool in = (a.flags & XY_IN_MIXED) != 0, out = (a.flags & XY_OUT_MIXED) != 0;
-    const size_t smem = (size_t)LY * (NX + 2) * sizeof(float2);
+    const size_t smem = (size_t)LY * (NX + 2) * sizeof(float2) + (NX + LY) * sizeof(Lift<float>);
     static bool cfg = false;      // one flag for all five variants of this shape
     if (!cfg) {
         const int sz = (int)smem;
@@ -698,7 +708,8 @@ template <int NZ, int ZA, int ZB, int P, int W>
 bool try_z(const ZArgs<float> &a, cudaStream_t st)
 {
     if (a.g.nz != NZ || a.g.P != P || a.g.w != W) return false;
-    const size_t smem = (size_t)NZ * P * W * sizeof(float2) + 2 * NZ * sizeof(Lift<float>);
+    const size_t smem = ((size_t)NZ * P * W + (P * W == 8 ? (NZ / 32) * 8 : 0)) * sizeof(float2) +
+                        2 * NZ * sizeof(Lift<float>);
     static bool cfg = false;
     if (!cfg) {
         cudaFuncSetAttribute(z_fast_kernel<NZ, ZA, ZB, P, W>,
