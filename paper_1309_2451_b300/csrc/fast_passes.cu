@@ -265,10 +265,18 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         }
     } else {
         __syncthreads();   // staged tables are read from here on
-        // natural rows into the swapped tile
-        for (int e = t; e < LY * NX; e += NT) {
-            const int jy = e / NX, x = e % NX;
-            sm[swy(jy) * PITCH + swx(x)] = src[((long long)(jy * g.P + r) << g.lgnx) + x];
+        // natural rows into the swapped tile: a task moves the RB consecutive
+        // points x = RB a + c of one row (16-byte loads); they land at swapped
+        // positions RA c + a, consecutive across the lanes (conflict-free)
+        for (int q = t; q < LY * RA; q += NT) {
+            const int a = q % RA, jy = q / RA;
+            const float2 *rowp = src + ((long long)(jy * g.P + r) << g.lgnx) + RB * a;
+            float2 *smr = sm + swy(jy) * PITCH + a;
+            float2 v[RB];
+#pragma unroll
+            for (int c = 0; c < RB; c += 2) ld2(rowp + c, v[c], v[c + 1]);
+#pragma unroll
+            for (int c = 0; c < RB; ++c) smr[RA * c] = v[c];
         }
     }
     __syncthreads();
@@ -438,9 +446,16 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
             });
         }
     } else {
-        for (int e = t; e < LY * NX; e += NT) {
-            const int jy = e / NX, x = e % NX;
-            dst[((long long)(jy * g.P + r) << g.lgnx) + x] = sm[swy(jy) * PITCH + swx(x)];
+        // natural rows out of the swapped tile (mirror of the natural load)
+        for (int q = t; q < LY * RA; q += NT) {
+            const int a = q % RA, jy = q / RA;
+            float2 *rowp = dst + ((long long)(jy * g.P + r) << g.lgnx) + RB * a;
+            const float2 *smr = sm + swy(jy) * PITCH + a;
+            float2 v[RB];
+#pragma unroll
+            for (int c = 0; c < RB; ++c) v[c] = smr[RA * c];
+#pragma unroll
+            for (int c = 0; c < RB; c += 2) st2(rowp + c, v[c], v[c + 1]);
         }
     }
 }
