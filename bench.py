@@ -35,7 +35,20 @@ METRIC = "3D split-step steps/s and HBM roofline % at 256x256x1024, FP32 vs FP64
 SHAPE = (1024, 256, 256)
 DT = 0.0025
 SPLIT = 50                 # split steps per bench step (one observation interval)
-SPLIT_FP64 = 2
+SPLIT_FP64 = 4
+FP64_PEAK_TFLOPS = 1.25    # nominal B300 FP64 rate (no measured figure on this machine)
+
+
+def pass_flops_per_point(shape, P):
+    """Algorithmic flops per point of one steady pass: 5 n log2 n per complex
+    FFT of length n (radix-2 count; forward and inverse), 6 per complex
+    product (the potential or kinetic factor).  XY: x over nx, partial y over
+    ny/P; Z: cross over P, z over nz."""
+    import math
+    nz, ny, nx = shape
+    xy = 2 * 5 * (math.log2(nx) + math.log2(ny // P)) + 6
+    z = 2 * 5 * (math.log2(P) + math.log2(nz)) + 6
+    return xy, z
 KERNEL_SOURCES = ["device_fft.cuh", "kernels.cuh", "kernels.cu", "fast_passes.cu"]
 
 
@@ -370,8 +383,18 @@ def run_ours(a):
         k64 = 0 if p64[0] >= p64[1] else 1
         avg64 = p64[k64] / max(c64[k64], 1)
         ach64 = 2 * N * 16 / (avg64 * 1e-3) / 1e9
+        P64 = r64["plan"].info()["row_classes"]
+        fxy, fz = pass_flops_per_point(SHAPE, P64)
+        tflops = (fxy if k64 == 0 else fz) * N / (avg64 * 1e-3) / 1e12
+        fast64 = r64["plan"].info()["fast_mask"]
         extra["fp64_path"] = {
             "steps_per_s": 1000.0 / ms64, "ms_per_step": ms64,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                         "peak_kind": "nominal FP64 (profiling recipe)",
+                         "kernel": ("xy_" if k64 == 0 else "z_") + ("fast" if fast64 else "pass")
+                                   + "_kernel<double>",
+                         "flops_per_point": fxy if k64 == 0 else fz},
             "hbm_frac_of_dominant_kernel": ach64 / hbm,
             "fp32_speedup": (1000.0 / (ms / (a.steps * SPLIT))) / (1000.0 / ms64),
             "dtype": "f64", "obs": [float(x) for x in r64["obs"]]}

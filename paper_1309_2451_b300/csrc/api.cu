@@ -148,8 +148,19 @@ ctap_status post_launch(PlanState &st, const char *what)
     } while (0)
 
 // ----------------------------------------------------------- table caches
+// Captured step graphs hold device pointers to tables and potentials: drop
+// them before any of those is freed or replaced.
+void drop_graphs(PlanState &st)
+{
+    if (!st.step_graphs.empty()) cudaStreamSynchronize(st.stream);
+    for (auto &g : st.step_graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    st.step_graphs.clear();
+}
+
 void drop_caches(PlanState &st)
 {
+    drop_graphs(st);
     for (auto &t : st.tabsets) {
         dev_free(t.kin);
         dev_free(t.sep);
@@ -159,6 +170,7 @@ void drop_caches(PlanState &st)
 
 void invalidate_sep(PlanState &st)
 {
+    drop_graphs(st);
     for (auto &t : st.tabsets) t.sep_valid = false;
 }
 
@@ -168,6 +180,7 @@ ctap_status get_tables(PlanState &st, double dt, int imag, TabSet **out)
     TabSet *hit = nullptr;
     for (auto &t : c)
         if (t.dt == dt && t.imag == imag) hit = &t;
+    if (!hit || (st.vform == VF_SEPARABLE && !hit->sep_valid)) drop_graphs(st);
     if (!hit) {
         if (c.size() >= 4) {
             dev_free(c.front().kin);
@@ -218,7 +231,8 @@ template <class T> XYArgs<T> xy_args(PlanState &st, const TabSet *ts, double dt,
     a.rd.k2h = st.d_k2h;
     a.vform_obs = st.vform;
     a.partials = st.d_partials;
-    a.small_angle = (st.vmax * std::fabs(dt) <= 0.5) ? 1 : 0;
+    // short kick series: |V| dt <= 0.5 (FP32 series) or <= 0.1 (FP64 series)
+    a.small_angle = (st.vmax * std::fabs(dt) <= (sizeof(T) == 4 ? 0.5 : 0.1)) ? 1 : 0;
     return a;
 }
 
@@ -242,8 +256,7 @@ template <class T> ctap_status go_xy(PlanState &st, const XYArgs<T> &a)
     bool done = false;
     // the fast XY pass moves two values per 16-byte access
     const bool aligned = ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15) == 0;
-    if constexpr (std::is_same<T, float>::value)
-        if (st.fast_xy && aligned) done = launch_xy_fast(a, st.stream);
+    if (st.fast_xy && aligned) done = launch_xy_fast(a, st.stream);
     if (!done) launch_xy<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "xy pass");
@@ -256,8 +269,7 @@ template <class T> ctap_status go_z(PlanState &st, const ZArgs<T> &a)
     bool done = false;
     // the fast Z pass moves two columns per 16-byte access
     const bool aligned = ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15) == 0;
-    if constexpr (std::is_same<T, float>::value)
-        if (st.fast_z && aligned) done = launch_z_fast(a, st.stream);
+    if (st.fast_z && aligned) done = launch_z_fast(a, st.stream);
     if (!done) launch_z<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "z pass");
@@ -313,6 +325,58 @@ template <class T> ctap_status run_steps(PlanState &st, Cx<T> *psi, int n, doubl
         CTAP_TRY(go_other(st, "scale", [&] { launch_scale<T>(psi, st.N, st.d_scale, st.stream); }));
     }
     return CTAP_OK;
+}
+
+// Replay a captured graph for a repeated (psi, n, dt, mode) call.  The first
+// call runs eagerly; the second captures the launch sequence once (tables are
+// uploaded before capture begins) and replays it; later calls replay.
+
+template <class T> ctap_status step_maybe_graph(PlanState &st, Cx<T> *psi, int n, double dt, int imag)
+{
+    const bool usable = st.graphs && st.stream != nullptr && !st.profiling &&
+                        !std::getenv("CTAP_FAULT_INJECT") && n > 0;
+    if (!usable) return run_steps<T>(st, psi, n, dt, imag);
+    for (auto &g : st.step_graphs) {
+        if (g.psi == psi && g.n == n && g.dt == dt && g.imag == imag) {
+            if (g.exec) {
+                cudaError_t e = cudaGraphLaunch(g.exec, st.stream);
+                if (e != cudaSuccess) return cuda_fail(st, e, "graph launch");
+                st.launches += g.launches;
+                return CTAP_OK;
+            }
+            // second sighting: capture
+            TabSet *ts = nullptr;
+            CTAP_TRY(get_tables(st, dt, imag, &ts));
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(st.stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(st, e, "begin capture");
+            const long long l0 = st.launches;
+            ctap_status s = run_steps<T>(st, psi, n, dt, imag);
+            cudaError_t e2 = cudaStreamEndCapture(st.stream, &graph);
+            if (s != CTAP_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
+            }
+            if (e2 != cudaSuccess) return cuda_fail(st, e2, "end capture");
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(st, e, "graph instantiate");
+            g.exec = exec;
+            g.launches = st.launches - l0;
+            st.launches = l0;
+            e = cudaGraphLaunch(exec, st.stream);
+            if (e != cudaSuccess) return cuda_fail(st, e, "graph launch");
+            st.launches += g.launches;
+            return CTAP_OK;
+        }
+    }
+    if (st.step_graphs.size() >= 8) {
+        if (st.step_graphs.front().exec) cudaGraphExecDestroy(st.step_graphs.front().exec);
+        st.step_graphs.erase(st.step_graphs.begin());
+    }
+    st.step_graphs.push_back(StepGraph{psi, n, dt, imag, nullptr, 0, 0});
+    return run_steps<T>(st, psi, n, dt, imag);
 }
 
 ctap_status ensure_work(PlanState &st)
@@ -479,6 +543,7 @@ ctap_status upload64(PlanState &st, double **d, const std::vector<double> &h)
 
 void clear_potential(PlanState &st)
 {
+    drop_graphs(st);
     dev_free(st.d_Vd);
     dev_free(st.d_g);
     dev_free(st.d_H);
@@ -514,6 +579,7 @@ ctap_status set_product(PlanState &st, const std::vector<double> &gy, const std:
 ctap_status set_guides_impl(PlanState &st, double V0, double s, const double *x1z,
                             const double *x3z, double hw, int set_regions)
 {
+    drop_graphs(st);
     if (!(s > 0) || !std::isfinite(V0) || !(hw > 0))
         return fail(st, CTAP_ERR_INVALID_ARG, "guides: need s > 0, finite V0, halfwidth > 0");
     const int nx = st.nx, ny = st.ny, nz = st.nz;
@@ -652,6 +718,7 @@ ctap_status ctap_plan_destroy(ctap_plan_t plan)
     if (!plan) return CTAP_ERR_INVALID_ARG;
     PlanState &st = plan->st;
     cudaStreamSynchronize(st.stream);
+    drop_graphs(st);
     drop_caches(st);
     clear_potential(st);
     dev_free(st.d_tw);
@@ -788,8 +855,8 @@ ctap_status ctap_step(ctap_plan_t plan, void *psi, int nsteps, double dt, ctap_t
     if (reinterpret_cast<uintptr_t>(psi) % st->esize) return fail(*st, CTAP_ERR_INVALID_ARG, "psi misaligned");
     const int imag = mode == CTAP_IMAG;
     if (st->dtype == CTAP_C64)
-        return run_steps<float>(*st, static_cast<float2 *>(psi), nsteps, dt, imag);
-    return run_steps<double>(*st, static_cast<double2 *>(psi), nsteps, dt, imag);
+        return step_maybe_graph<float>(*st, static_cast<float2 *>(psi), nsteps, dt, imag);
+    return step_maybe_graph<double>(*st, static_cast<double2 *>(psi), nsteps, dt, imag);
 }
 
 ctap_status ctap_observables(ctap_plan_t plan, const void *psi, double *out)

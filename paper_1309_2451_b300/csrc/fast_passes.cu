@@ -1,4 +1,4 @@
-// fast_passes.cu -- specialised complex64 XY and Z passes.
+// fast_passes.cu -- specialised XY and Z passes (complex64 and complex128).
 //
 // Same HBM layout and the same arithmetic definition as the generic passes
 // in kernels.cu (natural kx order, natural k' order, rows j P + r), so plans
@@ -59,13 +59,11 @@ __device__ __forceinline__ void lift_small(float th, float &p, float &u)
     p = -fmadd(h2 * h, t, h);
 }
 
-__device__ __forceinline__ void kick_one(float2 &v, float th, int imag, int small)
+// exp(-i th) for the real-time kick: the short series for complex64 when
+// |th| <= 0.5, the general half-turn reduction otherwise (always for FP64)
+__device__ __forceinline__ void kick_rt(float2 &v, float th, int small)
 {
-    if (imag) {
-        const float f = expf(-th);
-        v.x *= f;
-        v.y *= f;
-    } else if (small) {
+    if (small) {
         float p, u;
         lift_small(th, p, u);
         rot_f<float>(v, p, u);
@@ -77,19 +75,65 @@ __device__ __forceinline__ void kick_one(float2 &v, float th, int imag, int smal
         v.y *= s;
     }
 }
+// FP64: |th| <= 0.1 uses odd Taylor series without division (own; next
+// terms below 1e-18 relative), otherwise the general reduction.
+__device__ __forceinline__ void lift_small(double th, double &p, double &u)
+{
+    const double a = -th, a2 = a * a;
+    double s = fmadd(a2, -2.5052108385441720e-08, 2.7557319223985893e-06);   // -1/11!, 1/9!
+    s = fmadd(a2, s, -1.9841269841269841e-04);                               // -1/7!
+    s = fmadd(a2, s, 8.3333333333333333e-03);                                // 1/5!
+    s = fmadd(a2, s, -1.6666666666666667e-01);                               // -1/3!
+    u = fmadd(a2 * a, s, a);
+    const double h = 0.5 * a, h2 = h * h;
+    double t = fmadd(h2, 3.5921280365724810e-03, 8.8632355299021966e-03);    // 21844/6081075, 1382/155925
+    t = fmadd(h2, t, 2.1869488536155203e-02);                                // 62/2835
+    t = fmadd(h2, t, 5.3968253968253968e-02);                                // 17/315
+    t = fmadd(h2, t, 1.3333333333333333e-01);                                // 2/15
+    t = fmadd(h2, t, 3.3333333333333333e-01);                                // 1/3
+    p = -fmadd(h2 * h, t, h);
+}
 
-__device__ __forceinline__ void kick_sep(float2 &v, const Lift<float> &a, const Lift<float> &b,
-                                         const Lift<float> &c, int imag)
+__device__ __forceinline__ void kick_rt(double2 &v, double th, int small)
+{
+    if (small) {
+        double p, u;
+        lift_small(th, p, u);
+        rot_f<double>(v, p, u);
+        return;
+    }
+    double p, u, s;
+    lift_from_angle(-th, p, u, s);
+    rot_f<double>(v, p, u);
+    v.x *= s;
+    v.y *= s;
+}
+
+template <class T>
+__device__ __forceinline__ void kick_one(Cx<T> &v, T th, int imag, int small)
 {
     if (imag) {
-        const float f = a.f * b.f * c.f;
+        const T f = exp(-th);
         v.x *= f;
         v.y *= f;
     } else {
-        rot_f<float>(v, a.p, a.u);
-        rot_f<float>(v, b.p, b.u);
-        rot_f<float>(v, c.p, c.u);
-        const float s = a.s * b.s * c.s;
+        kick_rt(v, th, small);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void kick_sep(Cx<T> &v, const Lift<T> &a, const Lift<T> &b,
+                                         const Lift<T> &c, int imag)
+{
+    if (imag) {
+        const T f = a.f * b.f * c.f;
+        v.x *= f;
+        v.y *= f;
+    } else {
+        rot_f<T>(v, a.p, a.u);
+        rot_f<T>(v, b.p, b.u);
+        rot_f<T>(v, c.p, c.u);
+        const T s = a.s * b.s * c.s;
         v.x *= s;
         v.y *= s;
     }
@@ -97,25 +141,8 @@ __device__ __forceinline__ void kick_sep(float2 &v, const Lift<float> &a, const 
 
 // R consecutive complex values as R/2 128-bit shared-memory accesses
 // (p must be 16-byte aligned)
-template <int R> __device__ __forceinline__ void load_pairs(const float2 *p, float2 (&v)[R])
-{
-#pragma unroll
-    for (int i = 0; i < R; i += 2) {
-        const float4 w = *reinterpret_cast<const float4 *>(p + i);
-        v[i] = make_float2(w.x, w.y);
-        v[i + 1] = make_float2(w.z, w.w);
-    }
-}
-template <int R> __device__ __forceinline__ void store_pairs(float2 *p, const float2 (&v)[R])
-{
-#pragma unroll
-    for (int i = 0; i < R; i += 2)
-        *reinterpret_cast<float4 *>(p + i) = make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
-}
-// compiler-only fence: keeps table loads from being hoisted en masse (the
-// hoisted loads of a 32-point stage otherwise exceed the register file)
-__device__ __forceinline__ void hoist_fence() { asm volatile("" ::: "memory"); }
-
+// two consecutive complex64 values move as one 16-byte access; complex128
+// values are 16 bytes each already
 __device__ __forceinline__ void ld2(const float2 *p, float2 &a, float2 &b)
 {
     const float4 w = *reinterpret_cast<const float4 *>(p);
@@ -126,6 +153,29 @@ __device__ __forceinline__ void st2(float2 *p, const float2 &a, const float2 &b)
 {
     *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
+__device__ __forceinline__ void ld2(const double2 *p, double2 &a, double2 &b)
+{
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void st2(double2 *p, const double2 &a, const double2 &b)
+{
+    p[0] = a;
+    p[1] = b;
+}
+template <int R, class C2> __device__ __forceinline__ void load_pairs(const C2 *p, C2 (&v)[R])
+{
+#pragma unroll
+    for (int i = 0; i < R; i += 2) ld2(p + i, v[i], v[i + 1]);
+}
+template <int R, class C2> __device__ __forceinline__ void store_pairs(C2 *p, const C2 (&v)[R])
+{
+#pragma unroll
+    for (int i = 0; i < R; i += 2) st2(p + i, v[i], v[i + 1]);
+}
+// compiler-only fence: keeps table loads from being hoisted en masse (the
+// hoisted loads of a 32-point stage otherwise exceed the register file)
+__device__ __forceinline__ void hoist_fence() { asm volatile("" ::: "memory"); }
 
 template <int NQ, int NT = kFastNT> __device__ void block_sum(double (&acc)[NQ], double *out)
 {
@@ -155,35 +205,39 @@ template <int NQ, int NT = kFastNT> __device__ void block_sum(double (&acc)[NQ],
 // ======================================================================= XY
 // HOT: the steady real-time step with the product potential (full kick, no
 // reductions, small angles) compiled without per-point flag tests.
-template <int NX, int RA, int RB, int LY, int YA, int YB, bool IN_MIXED, bool OUT_MIXED,
+// threads per XY CTA: 512 for complex64, 256 for complex128 (register budget)
+template <class T> __host__ __device__ constexpr int xy_threads() { return sizeof(T) == 4 ? 512 : 256; }
+
+template <class T, int NX, int RA, int RB, int LY, int YA, int YB, bool IN_MIXED, bool OUT_MIXED,
           bool HOT>
-__global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
+__global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T> a)
 {
     static_assert(RA * RB == NX && YA * YB == LY, "radix split");
-    constexpr int NT = kFastNT;
+    using C2 = Cx<T>;
+    constexpr int NT = xy_threads<T>();
     constexpr int PITCH = NX + 2;          // even: rows stay 16-byte aligned
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *sm = reinterpret_cast<float2 *>(smraw);
-    __shared__ float gtab[LY];              // g(y), y = r + P jy
-    __shared__ float htab[NX];              // H(x, z) tau at swapped position
-    __shared__ Lift<float> ytab[LY];        // separable y factor
+    C2 *sm = reinterpret_cast<C2 *>(smraw);
+    __shared__ T gtab[LY];              // g(y), y = r + P jy
+    __shared__ T htab[NX];              // H(x, z) tau at swapped position
+    __shared__ Lift<T> ytab[LY];        // separable y factor
 
     const Geom &g = a.g;
     const int t = threadIdx.x;
     const int z = blockIdx.x >> g.lgP, r = blockIdx.x & (g.P - 1);
     const long long pbase = (long long)z * g.plane;
-    const float2 *src = a.src + pbase;
-    float2 *dst = a.dst + pbase;
+    const C2 *src = a.src + pbase;
+    C2 *dst = a.dst + pbase;
     // x and y twiddles staged in shared memory (after the tile)
-    Lift<float> *wx = reinterpret_cast<Lift<float> *>(sm + LY * PITCH);   // exp(-2 pi i e/NX)
-    Lift<float> *wy = wx + NX;                                            // exp(-2 pi i e/LY)
+    Lift<T> *wx = reinterpret_cast<Lift<T> *>(sm + LY * PITCH);   // exp(-2 pi i e/NX)
+    Lift<T> *wy = wx + NX;                                            // exp(-2 pi i e/LY)
     for (int e = t; e < NX + LY; e += NT)
         wx[e] = e < NX ? a.tw[g.fast_x_off + e] : a.tw[g.fast_y_off + e - NX];
     const int flags = HOT ? XY_KICK_FULL : a.flags;
-    const Kick<float> &k = a.k;
+    const Kick<T> &k = a.k;
     const bool kick = (flags & (XY_KICK_HALF | XY_KICK_FULL | XY_KICK_SPLIT)) != 0;
     const bool full = (flags & XY_KICK_FULL) != 0;
-    const float tau = full ? k.tau_full : k.tau_half;
+    const T tau = full ? k.tau_full : k.tau_half;
 
     auto swx = [](int x) { return RA * (x % RB) + x / RB; };     // natural x -> position
     auto unswx = [](int p) { return p / RA + RB * (p % RA); };   // position -> natural x
@@ -204,13 +258,13 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         {
             constexpr int NTASK = LY * RA;
             constexpr int Q = (NTASK + NT - 1) / NT;
-            float2 v[Q][RB];
+            C2 v[Q][RB];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int q = t + i * NT;
                 if (NTASK % NT == 0 || q < NTASK) {
                     const int j = q % RA, row = q / RA;
-                    const float2 *rowp = src + ((long long)(row * g.P + r) << g.lgnx);
+                    const C2 *rowp = src + ((long long)(row * g.P + r) << g.lgnx);
                     sfor<RB>([&](auto kc) {
                         constexpr int kk = decltype(kc)::value;
                         v[i][brev(kk, RB)] = rowp[j + RA * kk];
@@ -223,9 +277,9 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
                 const int q = t + i * NT;
                 if (NTASK % NT == 0 || q < NTASK) {
                     const int j = q % RA, row = q / RA;
-                    dft_inv<RB, 0, 1, float>(v[i]);
+                    dft_inv<RB, 0, 1, T>(v[i]);
 #pragma unroll
-                    for (int rr = 1; rr < RB; ++rr) lift_b<float>(v[i][rr], wx[j * rr]);
+                    for (int rr = 1; rr < RB; ++rr) lift_b<T>(v[i][rr], wx[j * rr]);
 #pragma unroll
                     for (int rr = 0; rr < RB; ++rr) sm[row * PITCH + j + RA * rr] = v[i][rr];
                 }
@@ -235,30 +289,30 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         // P2: inverse x, first stage (radix RA), in place on block j
         for (int q = t; q < LY * RB; q += NT) {
             const int row = q % LY, j = q / LY;
-            float2 *bp = sm + row * PITCH + RA * j;
-            float2 v[RA], w[RA];
+            C2 *bp = sm + row * PITCH + RA * j;
+            C2 v[RA], w[RA];
             load_pairs<RA>(bp, w);
 #pragma unroll
             for (int kk = 0; kk < RA; ++kk) v[brev(kk, RA)] = w[kk];
-            dft_inv<RA, 0, 1, float>(v);
+            dft_inv<RA, 0, 1, T>(v);
             store_pairs<RA>(bp, v);
         }
         __syncthreads();
         // P3a: inverse y, last stage (Ns = YA, radix YB), in place; two columns
         for (int q = t; q < (NX / 2) * YA; q += NT) {
             const int p = (q % (NX / 2)) * 2, i = q / (NX / 2);
-            float2 v[YB], w[YB];
+            C2 v[YB], w[YB];
             sfor<YB>([&](auto kc) {
                 constexpr int kk = decltype(kc)::value;
                 ld2(sm + (i + YA * kk) * PITCH + p, v[brev(kk, YB)], w[brev(kk, YB)]);
             });
-            dft_inv<YB, 0, 1, float>(v);
-            dft_inv<YB, 0, 1, float>(w);
+            dft_inv<YB, 0, 1, T>(v);
+            dft_inv<YB, 0, 1, T>(w);
 #pragma unroll
             for (int rr = 1; rr < YB; ++rr) {
-                const Lift<float> tw = wy[i * rr];
-                lift_b<float>(v[rr], tw);
-                lift_b<float>(w[rr], tw);
+                const Lift<T> tw = wy[i * rr];
+                lift_b<T>(v[rr], tw);
+                lift_b<T>(w[rr], tw);
             }
 #pragma unroll
             for (int rr = 0; rr < YB; ++rr) st2(sm + (i + YA * rr) * PITCH + p, v[rr], w[rr]);
@@ -270,9 +324,9 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         // positions RA c + a, consecutive across the lanes (conflict-free)
         for (int q = t; q < LY * RA; q += NT) {
             const int a = q % RA, jy = q / RA;
-            const float2 *rowp = src + ((long long)(jy * g.P + r) << g.lgnx) + RB * a;
-            float2 *smr = sm + swy(jy) * PITCH + a;
-            float2 v[RB];
+            const C2 *rowp = src + ((long long)(jy * g.P + r) << g.lgnx) + RB * a;
+            C2 *smr = sm + swy(jy) * PITCH + a;
+            C2 v[RB];
 #pragma unroll
             for (int c = 0; c < RB; c += 2) ld2(rowp + c, v[c], v[c + 1]);
 #pragma unroll
@@ -287,14 +341,14 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int q = t; q < (NX / 2) * YB; q += NT) {
             const int p0 = (q % (NX / 2)) * 2, i = q / (NX / 2);
-            float2 v[2][YA];
+            C2 v[2][YA];
             if constexpr (IN_MIXED) {
                 sfor<YA>([&](auto kc) {
                     constexpr int kk = decltype(kc)::value;
                     ld2(sm + (YA * i + kk) * PITCH + p0, v[0][brev(kk, YA)], v[1][brev(kk, YA)]);
                 });
-                dft_inv<YA, 0, 1, float>(v[0]);
-                dft_inv<YA, 0, 1, float>(v[1]);
+                dft_inv<YA, 0, 1, T>(v[0]);
+                dft_inv<YA, 0, 1, T>(v[1]);
             } else {
 #pragma unroll
                 for (int rr = 0; rr < YA; ++rr) ld2(sm + (YA * i + rr) * PITCH + p0, v[0][rr], v[1][rr]);
@@ -318,7 +372,7 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
 #pragma unroll
                     for (int rr = 0; rr < YA; ++rr) {
                         const int y = r + (i + YB * rr) * g.P;
-                        const float2 u = v[c][rr];
+                        const C2 u = v[c][rr];
                         const double d = (double)u.x * u.x + (double)u.y * u.y;
                         double V = 0.0;
                         if (a.vform_obs == VF_DENSE) V = (double)k.Vd[pbase + ((long long)y << g.lgnx) + x];
@@ -332,52 +386,49 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
                     }
                 }
                 if (HOT) {
-                    const float hx = htab[p];
+                    const T hx = htab[p];
 #pragma unroll
-                    for (int rr = 0; rr < YA; ++rr) {
-                        float pp, u;
-                        lift_small(gtab[i + YB * rr] * hx, pp, u);
-                        rot_f<float>(v[c][rr], pp, u);
-                    }
+                    for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], gtab[i + YB * rr] * hx, 1);
+                    // (the hot variant is only chosen when the short series applies)
                 } else if (kick) {
                     if (k.form == VF_SEPARABLE) {
-                        const Lift<float> *tb = full ? k.sep_full : k.sep_half;
-                        const Lift<float> lx = tb[x], lz = tb[g.nx + g.ny + z];
-                        const Lift<float> hx = k.sep_half[x], hz = k.sep_half[g.nx + g.ny + z];
+                        const Lift<T> *tb = full ? k.sep_full : k.sep_half;
+                        const Lift<T> lx = tb[x], lz = tb[g.nx + g.ny + z];
+                        const Lift<T> hx = k.sep_half[x], hz = k.sep_half[g.nx + g.ny + z];
 #pragma unroll
                         for (int rr = 0; rr < YA; ++rr) {
                             const int jy = i + YB * rr;
-                            kick_sep(v[c][rr], lx, ytab[jy], lz, k.imag);
+                            kick_sep<T>(v[c][rr], lx, ytab[jy], lz, k.imag);
                             if (flags & XY_RED_NORM)
                                 acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
                             if (flags & XY_KICK_SPLIT)
-                                kick_sep(v[c][rr], hx, k.sep_half[g.nx + r + jy * g.P], hz, k.imag);
+                                kick_sep<T>(v[c][rr], hx, k.sep_half[g.nx + r + jy * g.P], hz, k.imag);
                         }
                     } else {
                         const int small = a.small_angle;
-                        const float hx = (k.form == VF_PRODUCT) ? htab[p] : 0.f;
+                        const T hx = (k.form == VF_PRODUCT) ? htab[p] : T(0);
 #pragma unroll
                         for (int rr = 0; rr < YA; ++rr) {
                             const int jy = i + YB * rr;
-                            const float th =
+                            const T th =
                                 (k.form == VF_PRODUCT)
                                     ? gtab[jy] * hx
                                     : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
-                            kick_one(v[c][rr], th, k.imag, small);
+                            kick_one<T>(v[c][rr], th, k.imag, small);
                             if (flags & XY_RED_NORM)
                                 acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
-                            if (flags & XY_KICK_SPLIT) kick_one(v[c][rr], th, k.imag, small);
+                            if (flags & XY_KICK_SPLIT) kick_one<T>(v[c][rr], th, k.imag, small);
                         }
                     }
                 }
             }
             if constexpr (OUT_MIXED) {
-                dft_fwd<YA, 0, 1, float>(v[0]);
-                dft_fwd<YA, 0, 1, float>(v[1]);
+                dft_fwd<YA, 0, 1, T>(v[0]);
+                dft_fwd<YA, 0, 1, T>(v[1]);
                 sfor<YA>([&](auto kc) {
                     constexpr int kk = decltype(kc)::value;
                     st2(sm + (YA * i + kk) * PITCH + p0, v[0][brev(kk, YA)], v[1][brev(kk, YA)]);
@@ -388,10 +439,10 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
             }
         }
         if (!HOT) {
-            if (flags & XY_RED_OBS) block_sum<5>(acc, a.partials + (long long)blockIdx.x * 5);
+            if (flags & XY_RED_OBS) block_sum<5, NT>(acc, a.partials + (long long)blockIdx.x * 5);
             else if (flags & XY_RED_NORM) {
                 double n1[1] = {acc[0]};
-                block_sum<1>(n1, a.partials + blockIdx.x);
+                block_sum<1, NT>(n1, a.partials + blockIdx.x);
             }
         }
     }
@@ -401,17 +452,17 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         // P3c: forward y, last stage (Ns = YA, radix YB), in place; two columns
         for (int q = t; q < (NX / 2) * YA; q += NT) {
             const int p = (q % (NX / 2)) * 2, i = q / (NX / 2);
-            float2 v[YB], w[YB];
+            C2 v[YB], w[YB];
 #pragma unroll
             for (int rr = 0; rr < YB; ++rr) ld2(sm + (i + YA * rr) * PITCH + p, v[rr], w[rr]);
 #pragma unroll
             for (int rr = 1; rr < YB; ++rr) {
-                const Lift<float> tw = wy[i * rr];
-                lift_f<float>(v[rr], tw);
-                lift_f<float>(w[rr], tw);
+                const Lift<T> tw = wy[i * rr];
+                lift_f<T>(v[rr], tw);
+                lift_f<T>(w[rr], tw);
             }
-            dft_fwd<YB, 0, 1, float>(v);
-            dft_fwd<YB, 0, 1, float>(w);
+            dft_fwd<YB, 0, 1, T>(v);
+            dft_fwd<YB, 0, 1, T>(w);
             sfor<YB>([&](auto kc) {
                 constexpr int kk = decltype(kc)::value;
                 st2(sm + (i + YA * kk) * PITCH + p, v[brev(kk, YB)], w[brev(kk, YB)]);
@@ -421,10 +472,10 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         // P4: forward x, first stage (radix RA), in place on block j
         for (int q = t; q < LY * RB; q += NT) {
             const int row = q % LY, j = q / LY;
-            float2 *bp = sm + row * PITCH + RA * j;
-            float2 v[RA], w[RA];
+            C2 *bp = sm + row * PITCH + RA * j;
+            C2 v[RA], w[RA];
             load_pairs<RA>(bp, v);
-            dft_fwd<RA, 0, 1, float>(v);
+            dft_fwd<RA, 0, 1, T>(v);
 #pragma unroll
             for (int kk = 0; kk < RA; ++kk) w[kk] = v[brev(kk, RA)];
             store_pairs<RA>(bp, w);
@@ -433,13 +484,13 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         // P5: forward x, last stage (Ns = RA, radix RB), straight to HBM
         for (int q = t; q < LY * RA; q += NT) {
             const int j = q % RA, row = q / RA;
-            float2 v[RB];
+            C2 v[RB];
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) v[rr] = sm[row * PITCH + j + RA * rr];
 #pragma unroll
-            for (int rr = 1; rr < RB; ++rr) lift_f<float>(v[rr], wx[j * rr]);
-            dft_fwd<RB, 0, 1, float>(v);
-            float2 *rowp = dst + ((long long)(row * g.P + r) << g.lgnx);
+            for (int rr = 1; rr < RB; ++rr) lift_f<T>(v[rr], wx[j * rr]);
+            dft_fwd<RB, 0, 1, T>(v);
+            C2 *rowp = dst + ((long long)(row * g.P + r) << g.lgnx);
             sfor<RB>([&](auto kc) {
                 constexpr int kk = decltype(kc)::value;
                 rowp[j + RA * kk] = v[brev(kk, RB)];
@@ -449,9 +500,9 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
         // natural rows out of the swapped tile (mirror of the natural load)
         for (int q = t; q < LY * RA; q += NT) {
             const int a = q % RA, jy = q / RA;
-            float2 *rowp = dst + ((long long)(jy * g.P + r) << g.lgnx) + RB * a;
-            const float2 *smr = sm + swy(jy) * PITCH + a;
-            float2 v[RB];
+            C2 *rowp = dst + ((long long)(jy * g.P + r) << g.lgnx) + RB * a;
+            const C2 *smr = sm + swy(jy) * PITCH + a;
+            C2 v[RB];
 #pragma unroll
             for (int c = 0; c < RB; ++c) v[c] = smr[RA * c];
 #pragma unroll
@@ -463,19 +514,24 @@ __global__ void __launch_bounds__(kFastNT) xy_fast_kernel(const XYArgs<float> a)
 // ======================================================================== Z
 // threads per Z CTA: 1024-point lines hold 32 points per stage task and need
 // the 255-register budget of 256 threads; shorter lines fit 512 threads
-__host__ __device__ constexpr int z_threads(int nz) { return nz >= 1024 ? 256 : 512; }
+// (complex128 always uses 256)
+template <class T> __host__ __device__ constexpr int z_threads(int nz)
+{
+    return (sizeof(T) == 8 || nz >= 1024) ? 256 : 512;
+}
 
-template <int NZ, int ZA, int ZB, int P, int W>
-__global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
-    z_fast_kernel(const ZArgs<float> a)
+template <class T, int NZ, int ZA, int ZB, int P, int W>
+__global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 8) ? 2 : 1)
+    z_fast_kernel(const ZArgs<T> a)
 {
     static_assert(ZA * ZB == NZ, "NZ = ZA ZB");
-    constexpr int NT = z_threads(NZ);
+    using C2 = Cx<T>;
+    constexpr int NT = z_threads<T>(NZ);
     constexpr int C = P * W;
-    constexpr int V2 = (W >= 2) ? 2 : 1;               // columns per load task
+    constexpr int V2 = (sizeof(T) == 4 && W >= 2) ? 2 : 1;   // columns per load task
     static_assert(C >= 8, "tile needs at least 8 columns");
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    C2 *sm = reinterpret_cast<C2 *>(smraw);
     const Geom &g = a.g;
     const int t = threadIdx.x;
     const int kp = blockIdx.x >> g.nblk_lg, b = blockIdx.x & ((1 << g.nblk_lg) - 1);
@@ -484,27 +540,32 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
     // C == 8:  two rows share the 32 banks; rotate column pairs by z/2 (Z1/Z5)
     //          and shift every other block of 32 rows by half the banks (rows
     //          z and z + 32 meet in Z3): 8 padding slots after every 32 rows.
+    // complex128: a row of 8 values spans all 32 banks; rotate W-column blocks
+    //          by z so the lanes of Z1/Z5 (one column, 8 rows) spread out.
     auto at = [](int zz, int col) {
-        if constexpr (C >= 16) {
+        if constexpr (sizeof(T) == 8) {
+            constexpr int SWM = (W < 8) ? (8 / W - 1) : 0;
+            return zz * C + (col ^ ((zz & SWM) * W));
+        } else if constexpr (C >= 16) {
             constexpr int SWM = (W < 16) ? (16 / W - 1) : 0;
             return zz * C + (col ^ ((zz & SWM) * W));
         } else {
             return zz * C + (zz >> 5) * 8 + (col ^ (((zz >> 1) & 3) * 2));
         }
     };
-    const Lift<float> *wc = a.tw + g.cross_off;    // exp(-2 pi i e/ny)
+    const Lift<T> *wc = a.tw + g.cross_off;    // exp(-2 pi i e/ny)
     const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
     // z twiddles exp(-2 pi i e/NZ) and z kinetic factors, staged in shared
     // memory (L1 would lose them to the streaming tile loads)
-    constexpr int TILE = NZ * C + (C == 8 ? (NZ / 32) * 8 : 0);   // + row-block padding
-    Lift<float> *wz = reinterpret_cast<Lift<float> *>(sm + TILE);
-    Lift<float> *kz = wz + NZ;
+    constexpr int TILE = NZ * C + ((sizeof(T) == 4 && C == 8) ? (NZ / 32) * 8 : 0);   // + row-block padding
+    Lift<T> *wz = reinterpret_cast<Lift<T> *>(sm + TILE);
+    Lift<T> *kz = wz + NZ;
     for (int e = t; e < NZ; e += NT) {
         wz[e] = a.tw[g.fast_z_off + e];
         if (!a.observe) kz[e] = a.kin[g.nx + g.ny + e];
     }
 
-    Lift<float> cw[P];
+    Lift<T> cw[P];
 #pragma unroll
     for (int rr = 1; rr < P; ++rr) cw[rr] = wc[(rr * kp) & (g.ny - 1)];
 
@@ -514,13 +575,13 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
     {
         constexpr int NTASK = NZ * (W / V2);
         constexpr int Q = (NTASK + NT - 1) / NT;
-        float2 v[Q][V2][P];
+        C2 v[Q][V2][P];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int q = t + i * NT;
             if (NTASK % NT == 0 || q < NTASK) {
                 const int xo = (q % (W / V2)) * V2, zz = q / (W / V2);
-                const float2 *p = a.src + (long long)zz * g.plane + colbase + xo;
+                const C2 *p = a.src + (long long)zz * g.plane + colbase + xo;
 #pragma unroll
                 for (int rr = 0; rr < P; ++rr) {
                     if constexpr (V2 == 2) {
@@ -541,13 +602,13 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
 #pragma unroll
                 for (int c = 0; c < V2; ++c) {
 #pragma unroll
-                    for (int rr = 1; rr < P; ++rr) lift_f<float>(v[i][c][rr], cw[rr]);
-                    dft_fwd<P, 0, 1, float>(v[i][c]);
+                    for (int rr = 1; rr < P; ++rr) lift_f<T>(v[i][c][rr], cw[rr]);
+                    dft_fwd<P, 0, 1, T>(v[i][c]);
                 }
                 sfor<P>([&](auto kc) {
                     constexpr int k2 = decltype(kc)::value;
                     if constexpr (V2 == 2) {
-                        const float2 e0 = v[i][0][brev(k2, P)], e1 = v[i][1][brev(k2, P)];
+                        const C2 e0 = v[i][0][brev(k2, P)], e1 = v[i][1][brev(k2, P)];
                         *reinterpret_cast<float4 *>(sm + at(zz, k2 * W + xo)) =
                             make_float4(e0.x, e0.y, e1.x, e1.y);
                     } else {
@@ -562,10 +623,10 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
     // Z2: forward z, first stage (radix ZA) on rows j + ZB r, in place
     for (int q = t; q < C * ZB; q += NT) {
         const int col = q % C, j = q / C;
-        float2 v[ZA];
+        C2 v[ZA];
 #pragma unroll
         for (int rr = 0; rr < ZA; ++rr) v[rr] = sm[at(j + ZB * rr, col)];
-        dft_fwd<ZA, 0, 1, float>(v);
+        dft_fwd<ZA, 0, 1, T>(v);
         sfor<ZA>([&](auto kc) {
             constexpr int kk = decltype(kc)::value;
             sm[at(j + ZB * kk, col)] = v[brev(kk, ZA)];
@@ -575,56 +636,56 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
 
     // Z3: last stage on the contiguous rows ZB jp + j, kinetic factor, inverse
     {
-        const float sc = a.inv_n * (a.scale ? (float)(*a.scale) : 1.0f);
+        const T sc = a.inv_n * (a.scale ? (T)(*a.scale) : T(1));
         double acc[1] = {0.0};
         for (int q = t; q < C * ZA; q += NT) {
             const int col = q % C, jp = q / C;
             const int kx = b * W + (col % W);
             const int ky = kp + ((col / W) << g.lgLy);
-            float2 v[ZB];
+            C2 v[ZB];
 #pragma unroll
             for (int j = 0; j < ZB; ++j) v[j] = sm[at(ZB * jp + j, col)];
             sfor<ZB - 1>([&](auto jc) {
                 constexpr int j = decltype(jc)::value + 1;
                 if constexpr (j % 4 == 0) hoist_fence();
-                lift_f<float>(v[j], wz[jp * j]);
+                lift_f<T>(v[j], wz[jp * j]);
             });
-            dft_fwd<ZB, 0, 1, float>(v);
+            dft_fwd<ZB, 0, 1, T>(v);
             // register brev(k2) holds kz = jp + ZA k2
             if (a.observe) {
                 const double kxy = a.k2h[kx] + a.k2h[g.nx + ky];
                 sfor<ZB>([&](auto kc) {
                     constexpr int k2 = decltype(kc)::value;
-                    const float2 u = v[brev(k2, ZB)];
+                    const C2 u = v[brev(k2, ZB)];
                     acc[0] += (kxy + a.k2h[g.nx + g.ny + jp + ZA * k2]) *
                               ((double)u.x * u.x + (double)u.y * u.y);
                 });
                 continue;
             }
-            const Lift<float> ax = a.kin[kx], ay = a.kin[g.nx + ky];
+            const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky];
             sfor<ZB>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
                 if constexpr (k2 % 4 == 0) hoist_fence();
-                float2 &u = v[brev(k2, ZB)];
-                const Lift<float> az = kz[jp + ZA * k2];
+                C2 &u = v[brev(k2, ZB)];
+                const Lift<T> az = kz[jp + ZA * k2];
                 if (a.imag) {
-                    const float f = ax.f * ay.f * az.f * sc;
+                    const T f = ax.f * ay.f * az.f * sc;
                     u.x *= f;
                     u.y *= f;
                 } else {
-                    rot_f<float>(u, ax.p, ax.u);
-                    rot_f<float>(u, ay.p, ay.u);
-                    rot_f<float>(u, az.p, az.u);
-                    const float s = ax.s * ay.s * az.s * sc;
+                    rot_f<T>(u, ax.p, ax.u);
+                    rot_f<T>(u, ay.p, ay.u);
+                    rot_f<T>(u, az.p, az.u);
+                    const T s = ax.s * ay.s * az.s * sc;
                     u.x *= s;
                     u.y *= s;
                 }
             });
-            dft_inv<ZB, 0, 1, float>(v);
+            dft_inv<ZB, 0, 1, T>(v);
             sfor<ZB - 1>([&](auto jc) {
                 constexpr int j = decltype(jc)::value + 1;
                 if constexpr (j % 4 == 0) hoist_fence();
-                lift_b<float>(v[j], wz[jp * j]);
+                lift_b<T>(v[j], wz[jp * j]);
             });
 #pragma unroll
             for (int j = 0; j < ZB; ++j) sm[at(ZB * jp + j, col)] = v[j];
@@ -639,12 +700,12 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
     // Z4: inverse z, first stage, in place
     for (int q = t; q < C * ZB; q += NT) {
         const int col = q % C, j = q / C;
-        float2 v[ZA];
+        C2 v[ZA];
         sfor<ZA>([&](auto kc) {
             constexpr int kk = decltype(kc)::value;
             v[brev(kk, ZA)] = sm[at(j + ZB * kk, col)];
         });
-        dft_inv<ZA, 0, 1, float>(v);
+        dft_inv<ZA, 0, 1, T>(v);
 #pragma unroll
         for (int rr = 0; rr < ZA; ++rr) sm[at(j + ZB * rr, col)] = v[rr];
     }
@@ -653,7 +714,7 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
     // Z5: inverse cross DFT and store
     for (int q = t; q < NZ * (W / V2); q += NT) {
         const int xo = (q % (W / V2)) * V2, zz = q / (W / V2);
-        float2 v[V2][P];
+        C2 v[V2][P];
         sfor<P>([&](auto kc) {
             constexpr int k2 = decltype(kc)::value;
             if constexpr (V2 == 2) {
@@ -666,11 +727,11 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
         });
 #pragma unroll
         for (int c = 0; c < V2; ++c) {
-            dft_inv<P, 0, 1, float>(v[c]);
+            dft_inv<P, 0, 1, T>(v[c]);
 #pragma unroll
-            for (int rr = 1; rr < P; ++rr) lift_b<float>(v[c][rr], cw[rr]);
+            for (int rr = 1; rr < P; ++rr) lift_b<T>(v[c][rr], cw[rr]);
         }
-        float2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
+        C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
 #pragma unroll
         for (int rr = 0; rr < P; ++rr) {
             if constexpr (V2 == 2)
@@ -685,81 +746,105 @@ __global__ void __launch_bounds__(z_threads(NZ), (P * W == 8) ? 2 : 1)
 // ================================================================ dispatch
 namespace {
 
-template <int NX, int RA, int RB>
-bool try_xy(const XYArgs<float> &a, cudaStream_t st)
+template <class T, int NX, int RA, int RB, int LY, int YA, int YB>
+bool try_xy(const XYArgs<T> &a, cudaStream_t st)
 {
-    constexpr int LY = 64, YA = 8, YB = 8;
     if (a.g.nx != NX || a.g.Ly != LY) return false;
     const bool in = (a.flags & XY_IN_MIXED) != 0, out = (a.flags & XY_OUT_MIXED) != 0;
-    const size_t smem = (size_t)LY * (NX + 2) * sizeof(float2) + (NX + LY) * sizeof(Lift<float>);
+    const size_t smem = (size_t)LY * (NX + 2) * sizeof(Cx<T>) + (NX + LY) * sizeof(Lift<T>);
     static bool cfg = false;      // one flag for all five variants of this shape
     if (!cfg) {
         const int sz = (int)smem;
         const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, true>, attr, sz);
-        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, false>, attr, sz);
-        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, false, false>, attr, sz);
-        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, true, false>, attr, sz);
-        cudaFuncSetAttribute(xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, false, false>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, true>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, false>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, false, false>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, true, false>, attr, sz);
+        cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, false, false>, attr, sz);
         cfg = true;
     }
     const int grid = xy_grid(a.g);
+    constexpr int NT = xy_threads<T>();
     const bool hot = a.flags == (XY_IN_MIXED | XY_OUT_MIXED | XY_KICK_FULL) &&
                      a.k.form == VF_PRODUCT && !a.k.imag && a.small_angle;
     if (hot)
-        xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, true><<<grid, kFastNT, smem, st>>>(a);
+        xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, true><<<grid, NT, smem, st>>>(a);
     else if (in && out)
-        xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, true, false><<<grid, kFastNT, smem, st>>>(a);
+        xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, false><<<grid, NT, smem, st>>>(a);
     else if (in)
-        xy_fast_kernel<NX, RA, RB, LY, YA, YB, true, false, false><<<grid, kFastNT, smem, st>>>(a);
+        xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, false, false><<<grid, NT, smem, st>>>(a);
     else if (out)
-        xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, true, false><<<grid, kFastNT, smem, st>>>(a);
+        xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, true, false><<<grid, NT, smem, st>>>(a);
     else
-        xy_fast_kernel<NX, RA, RB, LY, YA, YB, false, false, false><<<grid, kFastNT, smem, st>>>(a);
+        xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, false, false><<<grid, NT, smem, st>>>(a);
     return true;
 }
 
-template <int NZ, int ZA, int ZB, int P, int W>
-bool try_z(const ZArgs<float> &a, cudaStream_t st)
+template <class T, int NZ, int ZA, int ZB, int P, int W>
+bool try_z(const ZArgs<T> &a, cudaStream_t st)
 {
     if (a.g.nz != NZ || a.g.P != P || a.g.w != W) return false;
-    const size_t smem = ((size_t)NZ * P * W + (P * W == 8 ? (NZ / 32) * 8 : 0)) * sizeof(float2) +
-                        2 * NZ * sizeof(Lift<float>);
+    constexpr int C = P * W;
+    const size_t tile = (size_t)NZ * C + ((sizeof(T) == 4 && C == 8) ? (NZ / 32) * 8 : 0);
+    const size_t smem = tile * sizeof(Cx<T>) + 2 * NZ * sizeof(Lift<T>);
     static bool cfg = false;
     if (!cfg) {
-        cudaFuncSetAttribute(z_fast_kernel<NZ, ZA, ZB, P, W>,
+        cudaFuncSetAttribute(z_fast_kernel<T, NZ, ZA, ZB, P, W>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cfg = true;
     }
-    z_fast_kernel<NZ, ZA, ZB, P, W><<<z_grid(a.g), z_threads(NZ), smem, st>>>(a);
+    z_fast_kernel<T, NZ, ZA, ZB, P, W><<<z_grid(a.g), z_threads<T>(NZ), smem, st>>>(a);
     return true;
 }
 
 }  // namespace
 
-bool fast_xy_supported(int nx, int Ly)
+// Rows per XY tile of the specialised passes: 64 for complex64, 32 for
+// complex128 (a tile is then 128 KB either way).
+int fast_rows(int esize) { return esize == 8 ? 64 : 32; }
+
+bool fast_xy_supported(int esize, int nx, int Ly)
 {
-    return Ly == 64 && (nx == 256 || nx == 128 || nx == 64);
+    return Ly == fast_rows(esize) && (nx == 256 || nx == 128 || nx == 64);
 }
 
-bool fast_z_supported(int nz, int P, int w)
+bool fast_z_supported(int esize, int nz, int P, int w)
 {
-    return (nz == 1024 && ((P == 4 && w == 4) || (P == 1 && w == 16) || (P == 2 && w == 8))) ||
-           (nz == 512 && ((P == 4 && w == 8) || (P == 2 && w == 16))) ||
-           (nz == 256 && ((P == 4 && w == 16) || (P == 2 && w == 32) || (P == 1 && w == 64)));
+    if (esize == 8)
+        return (nz == 1024 && ((P == 4 && w == 4) || (P == 1 && w == 16) || (P == 2 && w == 8))) ||
+               (nz == 512 && ((P == 4 && w == 8) || (P == 2 && w == 16))) ||
+               (nz == 256 && ((P == 4 && w == 16) || (P == 2 && w == 32) || (P == 1 && w == 64)));
+    return (nz == 1024 && ((P == 8 && w == 1) || (P == 2 && w == 4) || (P == 4 && w == 2))) ||
+           (nz == 512 && ((P == 8 && w == 2) || (P == 4 && w == 4))) ||
+           (nz == 256 && ((P == 8 && w == 4) || (P == 4 && w == 8)));
 }
 
 bool launch_xy_fast(const XYArgs<float> &a, cudaStream_t st)
 {
-    return try_xy<256, 16, 16>(a, st) || try_xy<128, 16, 8>(a, st) || try_xy<64, 8, 8>(a, st);
+    return try_xy<float, 256, 16, 16, 64, 8, 8>(a, st) || try_xy<float, 128, 16, 8, 64, 8, 8>(a, st) ||
+           try_xy<float, 64, 8, 8, 64, 8, 8>(a, st);
+}
+
+bool launch_xy_fast(const XYArgs<double> &a, cudaStream_t st)
+{
+    return try_xy<double, 256, 16, 16, 32, 4, 8>(a, st) ||
+           try_xy<double, 128, 16, 8, 32, 4, 8>(a, st) || try_xy<double, 64, 8, 8, 32, 4, 8>(a, st);
 }
 
 bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st)
 {
-    return try_z<1024, 32, 32, 4, 4>(a, st) || try_z<1024, 32, 32, 1, 16>(a, st) ||
-           try_z<1024, 32, 32, 2, 8>(a, st) || try_z<512, 32, 16, 4, 8>(a, st) ||
-           try_z<512, 32, 16, 2, 16>(a, st) || try_z<256, 16, 16, 4, 16>(a, st) ||
-           try_z<256, 16, 16, 2, 32>(a, st) || try_z<256, 16, 16, 1, 64>(a, st);
+    return try_z<float, 1024, 32, 32, 4, 4>(a, st) || try_z<float, 1024, 32, 32, 1, 16>(a, st) ||
+           try_z<float, 1024, 32, 32, 2, 8>(a, st) || try_z<float, 512, 32, 16, 4, 8>(a, st) ||
+           try_z<float, 512, 32, 16, 2, 16>(a, st) || try_z<float, 256, 16, 16, 4, 16>(a, st) ||
+           try_z<float, 256, 16, 16, 2, 32>(a, st) || try_z<float, 256, 16, 16, 1, 64>(a, st);
+}
+
+bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st)
+{
+    return try_z<double, 1024, 32, 32, 8, 1>(a, st) || try_z<double, 1024, 32, 32, 2, 4>(a, st) ||
+           try_z<double, 1024, 32, 32, 4, 2>(a, st) || try_z<double, 512, 32, 16, 8, 2>(a, st) ||
+           try_z<double, 512, 32, 16, 4, 4>(a, st) || try_z<double, 256, 16, 16, 8, 4>(a, st) ||
+           try_z<double, 256, 16, 16, 4, 8>(a, st);
 }
 
 }  // namespace ctap

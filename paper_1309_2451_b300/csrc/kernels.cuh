@@ -126,11 +126,15 @@ template <class T> void launch_grad(const Cx<T> *lam, const Cx<T> *psi, const Ge
                                     double c, double *R1, double *R3, cudaStream_t st);
 int mask_blocks(const Geom &g);
 
-// fast_passes.cu: specialised complex64 passes (same layout as the generic
-// ones); the launchers return false when the geometry is not covered.
-bool fast_xy_supported(int nx, int Ly);
-bool fast_z_supported(int nz, int P, int w);
+// fast_passes.cu: specialised passes (same layout as the generic ones); the
+// launchers return false when the geometry is not covered.  esize is the
+// size of one complex value (8 or 16).
+int fast_rows(int esize);
+bool fast_xy_supported(int esize, int nx, int Ly);
+bool fast_z_supported(int esize, int nz, int P, int w);
 bool launch_xy_fast(const XYArgs<float> &a, cudaStream_t st);
+bool launch_xy_fast(const XYArgs<double> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st);
+bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st);
 
 }  // namespace ctap

@@ -25,6 +25,17 @@ struct TabSet {
     bool sep_valid;
 };
 
+// an instantiated CUDA graph of one ctap_step call
+struct StepGraph {
+    void *psi;
+    int n;
+    double dt;
+    int imag;
+    cudaGraphExec_t exec;
+    long long launches;
+    long long uses;
+};
+
 struct PlanState {
     // grid
     int nx, ny, nz;
@@ -82,6 +93,10 @@ struct PlanState {
     size_t events_used = 0;
     long long prof_counts[3] = {0, 0, 0};
     double prof_ms[3] = {0, 0, 0};
+
+    // CUDA graphs of repeated ctap_step calls (non-default streams only)
+    bool graphs = true;
+    std::vector<StepGraph> step_graphs;
 
     std::string err;
 };

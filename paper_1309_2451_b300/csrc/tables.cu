@@ -102,9 +102,10 @@ void build_geometry(PlanState &p, int emax, int maxv)
     while ((long long)p.nx * p.ny / P > emax) P *= 2;
     p.fast_xy = false;
     p.fast_z = false;
-    if (p.dtype == CTAP_C64 && !p.force_generic && p.ny >= 64 && fast_xy_supported(p.nx, 64) &&
-        p.ny / 64 <= 16) {
-        P = p.ny / 64;                       // y-lines of 64 points held in registers
+    const int LYF = fast_rows(p.esize);
+    if (!p.force_generic && p.ny >= LYF && fast_xy_supported(p.esize, p.nx, LYF) &&
+        p.ny / LYF <= 16) {
+        P = p.ny / LYF;                      // row classes of the specialised XY pass
         p.fast_xy = true;
     }
     if (P > 16 || P > p.ny) throw std::runtime_error("xy-plane too large for the row-class split");
@@ -115,7 +116,7 @@ void build_geometry(PlanState &p, int emax, int maxv)
     g.P = P;
     g.Ly = p.ny / P;
     g.w = w;
-    if (p.dtype == CTAP_C64 && !p.force_generic && fast_z_supported(p.nz, P, w)) p.fast_z = true;
+    if (!p.force_generic && fast_z_supported(p.esize, p.nz, P, w)) p.fast_z = true;
     g.C = w * P;
     g.lgnx = lg2(p.nx);
     g.lgny = lg2(p.ny);

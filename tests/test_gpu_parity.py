@@ -270,6 +270,41 @@ def test_zero_steps_is_identity_and_runs_are_deterministic(ctap):
     assert np.array_equal(plan.observables(a), plan.observables(b))
 
 
+def test_step_graphs_replay_bitwise_and_invalidate(ctap):
+    """Repeated ctap_step calls on a non-default stream are captured once and
+    replayed as a CUDA graph; the result must be bitwise that of the eager
+    launches (legacy stream, no graphs), and a potential change after the
+    capture must not leave a stale graph."""
+    shape, box = (64, 64, 64), wl.CTAP_BOX
+    z = wl.axis(64, box[4], box[5])
+    c = wl.guide_centres(z)
+    psi0 = to_dev(wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=13), "c64")
+    side = torch.cuda.Stream()
+    pg = ctap.Plan(shape, box, "c64", stream=side)
+    pe = ctap.Plan(shape, box, "c64", stream=torch.cuda.default_stream())
+    for p in (pg, pe):
+        p.set_guides(wl.V0, 1.0, c[0], c[2], 1.5)
+    a, b = psi0.clone(), psi0.clone()
+    torch.cuda.synchronize()
+    for _ in range(4):
+        n0 = pg.launch_count
+        pg.step(a, 5, 0.005)
+        assert pg.launch_count - n0 == 11          # 2 n + 1 kernels, replayed or not
+        pe.step(b, 5, 0.005)
+    side.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    # change the potential: a captured graph must not survive
+    pg.set_guides(wl.V0 * 0.5, 1.0, c[0], c[2], 1.5)
+    pe.set_guides(wl.V0 * 0.5, 1.0, c[0], c[2], 1.5)
+    for _ in range(3):
+        pg.step(a, 5, 0.005)
+        pe.step(b, 5, 0.005)
+    side.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
 def test_errors_are_reported(ctap):
     shape, box = (8, 8, 8), (-1.0, 1.0, -1.0, 1.0, -1.0, 1.0)
     plan = ctap.Plan(shape, box, "c64")
@@ -319,6 +354,27 @@ def test_fast_and_generic_passes_match_oracle(ctap, shape, monkeypatch):
     obs_f = plan.observables(to_dev(psi0, "c64"))
     obs_g = gplan.observables(to_dev(psi0, "c64"))
     assert np.allclose(obs_f, obs_g, rtol=1e-6, atol=1e-9)
+
+
+FAST128_SHAPES = [(256, 128, 128), (256, 256, 256), (512, 256, 256), (1024, 128, 256),
+                  (64, 64, 64), (16, 32, 128)]
+
+
+@pytest.mark.parametrize("shape", FAST128_SHAPES)
+def test_fast_passes_complex128_match_oracle(ctap, shape):
+    """The specialised passes in FP64 (32-row XY classes, 8-column Z tiles)."""
+    box = wl.CTAP_BOX
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=6) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    plan, V, c = guides_plan(ctap, shape, box, "c128")
+    assert plan.info()["fast_mask"] & 1, plan.info()
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 3, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, 3)
+    assert rel(psi.cpu().numpy(), ref) < 1e-13
+    got = plan.observables(psi)
+    ref_obs = oracle.observables(ref, V, box, c, wl.POP_HALFWIDTH)
+    assert np.allclose(got, ref_obs, rtol=1e-11, atol=1e-14)
 
 
 def test_fast_passes_long_run(ctap):
