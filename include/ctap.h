@@ -146,9 +146,11 @@ ctap_status ctap_set_timeout(ctap_plan_t plan, int timeout_ms);
 ctap_status ctap_launch_count(ctap_plan_t plan, long long *count);
 
 /* Per-pass timing with CUDA events on the plan stream.  When enabled, every
- * launch of ctap_step is bracketed by events; ctap_pass_times writes, per
- * pass kind (0 prologue/epilogue/xy, 1 z, 2 other), the number of launches
- * and the summed milliseconds since the last reset (synchronises). */
+ * launch of ctap_step / ctap_observables is bracketed by events;
+ * ctap_pass_times writes, per pass kind (0 steady XY pass, 1 Z pass, 2 every
+ * other launch: prologue/epilogue/observe XY passes, reductions), the number
+ * of launches and the summed milliseconds since the last call (synchronises).
+ * Graph replay is disabled while profiling is on. */
 ctap_status ctap_set_profiling(ctap_plan_t plan, int enable);
 ctap_status ctap_pass_times(ctap_plan_t plan, long long counts[3], double ms[3]);
 

@@ -252,7 +252,9 @@ template <class T> ZArgs<T> z_args(PlanState &st, const TabSet *ts, int imag)
 template <class T> ctap_status go_xy(PlanState &st, const XYArgs<T> &a)
 {
     CTAP_TRY(pre_launch(st));
-    int ev = prof_begin(st, 0);
+    // kind 0: the steady XY pass; prologue/epilogue/observe variants count as 2
+    const bool steady = (a.flags & (XY_IN_MIXED | XY_OUT_MIXED)) == (XY_IN_MIXED | XY_OUT_MIXED);
+    int ev = prof_begin(st, steady ? 0 : 2);
     bool done = false;
     // the fast XY pass moves two values per 16-byte access
     const bool aligned = ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15) == 0;
@@ -425,28 +427,98 @@ ctap_status finish_observables(PlanState &st, const double *raw, double *out)
 }
 
 // ------------------------------------------------------------- adjoint
+// Recompute the states of one checkpoint segment: from psi_{n0} (natural,
+// copied into `work`), L steps; the steady XY pass writes psi_{n0+i} to
+// states[i] between its two half-kicks, the last pass writes psi_{n0+L} to
+// states[L].  2 L + 1 launches, no copies.
+template <class T>
+ctap_status record_segment(PlanState &st, Cx<T> *work, int L, double dt, Cx<T> *const *states)
+{
+    TabSet *ts = nullptr;
+    CTAP_TRY(get_tables(st, dt, 0, &ts));
+    XYArgs<T> xa = xy_args<T>(st, ts, dt, 0);
+    ZArgs<T> za = z_args<T>(st, ts, 0);
+    xa.src = xa.dst = work;
+    za.src = za.dst = work;
+    xa.flags = XY_KICK_HALF | XY_OUT_MIXED;
+    CTAP_TRY(go_xy<T>(st, xa));
+    for (int s = 0; s < L; ++s) {
+        CTAP_TRY(go_z<T>(st, za));
+        if (s + 1 < L) {
+            xa.flags = XY_IN_MIXED | XY_KICK_SPLIT | XY_STATE_OUT | XY_OUT_MIXED;
+            xa.state_out = states[s + 1];
+            CTAP_TRY(go_xy<T>(st, xa));
+        }
+    }
+    xa.flags = XY_IN_MIXED | XY_KICK_HALF;
+    xa.dst = states[L];
+    return go_xy<T>(st, xa);
+}
+
+// Sweep lambda back over one segment: lambda_{n1} (natural, in place) ->
+// lambda_{n0} with steps of -dt (S(-dt) is the adjoint of S(dt)).  Each XY
+// pass adds dt w_m sum Im(conj(lambda_m) psi_m) dV/dx_j to the per-CTA
+// partials at the integer step it holds: the first pass at m = n1 (its
+// input), the steady passes between their half-kicks, the last pass (only
+// when `bottom`) at m = n0.  psi[i] is psi_{n0+i}.
+template <class T>
+ctap_status lambda_segment(PlanState &st, Cx<T> *lam, int L, double dt, const Cx<T> *const *psi,
+                           double coef_top, bool bottom, double coef_bottom, double *acc)
+{
+    TabSet *ts = nullptr;
+    CTAP_TRY(get_tables(st, -dt, 0, &ts));
+    XYArgs<T> xa = xy_args<T>(st, ts, -dt, 0);
+    ZArgs<T> za = z_args<T>(st, ts, 0);
+    xa.src = xa.dst = lam;
+    za.src = za.dst = lam;
+    xa.gd.g64 = st.d_g64;
+    xa.gd.D1 = st.d_D1;
+    xa.gd.D3 = st.d_D3;
+    xa.gd.acc = acc;
+    const double interior = 2.0 * dt * st.dV;
+    xa.flags = XY_KICK_HALF | XY_OUT_MIXED | XY_GRAD_PRE;
+    xa.gd.psi = psi[L];
+    xa.gd.coef = coef_top;
+    CTAP_TRY(go_xy<T>(st, xa));
+    for (int s = 0; s < L; ++s) {
+        CTAP_TRY(go_z<T>(st, za));
+        if (s + 1 < L) {
+            xa.flags = XY_IN_MIXED | XY_KICK_SPLIT | XY_GRAD | XY_OUT_MIXED;
+            xa.gd.psi = psi[L - 1 - s];
+            xa.gd.coef = interior;
+            CTAP_TRY(go_xy<T>(st, xa));
+        }
+    }
+    xa.flags = XY_IN_MIXED | XY_KICK_HALF | (bottom ? XY_GRAD : 0);
+    xa.gd.psi = psi[0];
+    xa.gd.coef = coef_bottom;
+    return go_xy<T>(st, xa);
+}
+
 template <class T>
 ctap_status run_adjoint(PlanState &st, const Cx<T> *psi0, int nsteps, double dt, int K, int guide,
                         double *J, double *grad)
 {
     const size_t bytes = (size_t)st.N * sizeof(Cx<T>);
     const int nseg = (nsteps + K - 1) / K;
+    const int Kseg = std::min(K, nsteps);
+    const int nacc = xy_grid(st.geom);
     struct Bufs {
-        void *cp = nullptr, *seg = nullptr, *cur = nullptr, *lam = nullptr, *R = nullptr;
+        void *cp = nullptr, *seg = nullptr, *work = nullptr, *lam = nullptr, *acc = nullptr;
         ~Bufs()
         {
             dev_free(cp);
             dev_free(seg);
-            dev_free(cur);
+            dev_free(work);
             dev_free(lam);
-            dev_free(R);
+            dev_free(acc);
         }
     } b;
     CTAP_TRY(dev_alloc(st, &b.cp, bytes * nseg));
-    CTAP_TRY(dev_alloc(st, &b.seg, bytes * (K + 1)));
-    CTAP_TRY(dev_alloc(st, &b.cur, bytes));
+    CTAP_TRY(dev_alloc(st, &b.seg, bytes * Kseg));
+    CTAP_TRY(dev_alloc(st, &b.work, bytes));
     CTAP_TRY(dev_alloc(st, &b.lam, bytes));
-    CTAP_TRY(dev_alloc(st, &b.R, sizeof(double) * 2 * st.nz));
+    CTAP_TRY(dev_alloc(st, &b.acc, sizeof(double) * 2 * nacc));
     auto at = [&](void *base, size_t i) {
         return reinterpret_cast<Cx<T> *>(static_cast<char *>(base) + i * bytes);
     };
@@ -454,17 +526,16 @@ ctap_status run_adjoint(PlanState &st, const Cx<T> *psi0, int nsteps, double dt,
         cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st.stream);
         return e == cudaSuccess ? CTAP_OK : cuda_fail(st, e, "copy");
     };
-    double *R1 = static_cast<double *>(b.R), *R3 = R1 + st.nz;
-    if (cudaMemsetAsync(b.R, 0, sizeof(double) * 2 * st.nz, st.stream) != cudaSuccess)
+    double *acc = static_cast<double *>(b.acc);
+    if (cudaMemsetAsync(acc, 0, sizeof(double) * 2 * nacc, st.stream) != cudaSuccess)
         return fail(st, CTAP_ERR_CUDA, "memset");
 
     // forward sweep with checkpoints psi_{sK}
-    Cx<T> *cur = at(b.cur, 0);
+    Cx<T> *cur = at(b.work, 0);
     CTAP_TRY(copy(cur, psi0));
     for (int s = 0; s < nseg; ++s) {
         CTAP_TRY(copy(at(b.cp, s), cur));
-        const int len = std::min(K, nsteps - s * K);
-        CTAP_TRY(run_steps<T>(st, cur, len, dt, 0));
+        CTAP_TRY(run_steps<T>(st, cur, std::min(K, nsteps - s * K), dt, 0));
     }
     // J and lambda_N = M psi_N
     Cx<T> *lam = at(b.lam, 0);
@@ -475,41 +546,42 @@ ctap_status run_adjoint(PlanState &st, const Cx<T> *psi0, int nsteps, double dt,
     }));
     CTAP_TRY(go_other(st, "reduce", [&] { launch_reduce(st.d_partials, nmb, 1, st.d_red, st.stream); }));
 
-    // backward sweep: lambda_n = S(-dt) lambda_{n+1}; states recomputed per segment
+    // backward sweep, one checkpoint segment at a time
+    std::vector<Cx<T> *> states(Kseg + 1);
     for (int s = nseg - 1; s >= 0; --s) {
-        const int n0 = s * K, n1 = std::min((s + 1) * K, nsteps);
-        CTAP_TRY(copy(at(b.seg, 0), at(b.cp, s)));
-        for (int i = 1; i <= n1 - n0; ++i) {
-            CTAP_TRY(copy(at(b.seg, i), at(b.seg, i - 1)));
-            CTAP_TRY(run_steps<T>(st, at(b.seg, i), 1, dt, 0));
-        }
-        const int nlo = (s == 0) ? 0 : n0 + 1;
-        for (int n = n1; n >= nlo; --n) {
-            const double w = (n == 0 || n == nsteps) ? 1.0 : 2.0;
-            const Cx<T> *psin = at(b.seg, n - n0);
-            CTAP_TRY(go_other(st, "grad", [&] {
-                launch_grad<T>(lam, psin, st.geom, st.d_g64, st.d_D1, st.d_D3, dt * w * st.dV, R1,
-                               R3, st.stream);
-            }));
-            if (n > 0) CTAP_TRY(run_steps<T>(st, lam, 1, -dt, 0));
-        }
+        const int n0 = s * K, n1 = std::min((s + 1) * K, nsteps), L = n1 - n0;
+        states[0] = at(b.cp, s);
+        for (int i = 1; i <= L; ++i) states[i] = at(b.seg, i - 1);
+        CTAP_TRY(copy(cur, states[0]));
+        CTAP_TRY(record_segment<T>(st, cur, L, dt, states.data()));
+        const double wtop = (n1 == nsteps) ? 1.0 : 2.0;
+        CTAP_TRY(lambda_segment<T>(st, lam, L, dt, states.data(), dt * wtop * st.dV, s == 0,
+                                   dt * st.dV, acc));
     }
-    std::vector<double> hR(2 * st.nz);
+    std::vector<double> hacc(2 * (size_t)nacc);
     double hJ = 0.0;
-    if (cudaMemcpyAsync(hR.data(), b.R, sizeof(double) * 2 * st.nz, cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(hacc.data(), acc, sizeof(double) * 2 * nacc, cudaMemcpyDeviceToHost,
                         st.stream) != cudaSuccess ||
         cudaMemcpyAsync(&hJ, st.d_red, sizeof(double), cudaMemcpyDeviceToHost, st.stream) !=
             cudaSuccess)
         return fail(st, CTAP_ERR_CUDA, "adjoint copy");
     CTAP_TRY(wait_stream(st, 0));
     *J = hJ * st.dV;
+    // per-slice sensitivities R_j(z): sum over the row classes of the plane
+    const int P = st.geom.P;
+    std::vector<double> R1(st.nz, 0.0), R3(st.nz, 0.0);
+    for (int z = 0; z < st.nz; ++z)
+        for (int r = 0; r < P; ++r) {
+            R1[z] += hacc[2 * ((size_t)z * P + r)];
+            R3[z] += hacc[2 * ((size_t)z * P + r) + 1];
+        }
     const int m = (int)st.knots.size();
     for (int k = 0; k < m; ++k) {
         double g12 = 0.0, g23 = 0.0;
         for (int z = 0; z < st.nz; ++z) {
             const double B = st.basis[(size_t)k * st.nz + z];
-            g12 -= B * hR[z];               // x_1 = -d12
-            g23 += B * hR[st.nz + z];       // x_3 = +d23
+            g12 -= B * R1[z];               // x_1 = -d12
+            g23 += B * R3[z];               // x_3 = +d23
         }
         grad[k] = g12;
         grad[m + k] = g23;

@@ -339,6 +339,20 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
     // two adjacent column positions per task
     {
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        double gacc[2] = {0.0, 0.0};
+        // adjoint gradient partial of one task: sum_y Im(conj(v) psi) g(y), times D_j(z,x)
+        auto grad_task = [&](const C2 (&vv)[YA], int i, int x) {
+            const C2 *ps = static_cast<const C2 *>(a.gd.psi) + pbase + x;
+            double t1 = 0.0;
+#pragma unroll
+            for (int rr = 0; rr < YA; ++rr) {
+                const int y = r + (i + YB * rr) * g.P;
+                const C2 q = ps[(long long)y << g.lgnx];
+                t1 += ((double)vv[rr].x * q.y - (double)vv[rr].y * q.x) * a.gd.g64[y];
+            }
+            gacc[0] += t1 * a.gd.D1[(long long)z * g.nx + x];
+            gacc[1] += t1 * a.gd.D3[(long long)z * g.nx + x];
+        };
         for (int q = t; q < (NX / 2) * YB; q += NT) {
             const int p0 = (q % (NX / 2)) * 2, i = q / (NX / 2);
             C2 v[2][YA];
@@ -385,6 +399,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
                         acc[4] += in2 ? d : 0.0;
                     }
                 }
+                if (!HOT && (flags & XY_GRAD_PRE)) grad_task(v[c], i, x);
                 if (HOT) {
                     const T hx = htab[p];
 #pragma unroll
@@ -403,8 +418,13 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
                                 acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
-                            if (flags & XY_KICK_SPLIT)
-                                kick_sep<T>(v[c][rr], hx, k.sep_half[g.nx + r + jy * g.P], hz, k.imag);
+                        }
+                        if (flags & XY_GRAD) grad_task(v[c], i, x);
+                        if (flags & XY_KICK_SPLIT) {
+#pragma unroll
+                            for (int rr = 0; rr < YA; ++rr)
+                                kick_sep<T>(v[c][rr], hx, k.sep_half[g.nx + r + (i + YB * rr) * g.P], hz,
+                                            k.imag);
                         }
                     } else {
                         const int small = a.small_angle;
@@ -421,7 +441,17 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
                                 acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
-                            if (flags & XY_KICK_SPLIT) kick_one<T>(v[c][rr], th, k.imag, small);
+                        }
+                        if (flags & XY_GRAD) grad_task(v[c], i, x);
+                        if (flags & XY_KICK_SPLIT) {
+#pragma unroll
+                            for (int rr = 0; rr < YA; ++rr) {
+                                const int jy = i + YB * rr;
+                                const T th = (k.form == VF_PRODUCT)
+                                                 ? gtab[jy] * hx
+                                                 : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
+                                kick_one<T>(v[c][rr], th, k.imag, small);
+                            }
                         }
                     }
                 }
@@ -443,6 +473,15 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
             else if (flags & XY_RED_NORM) {
                 double n1[1] = {acc[0]};
                 block_sum<1, NT>(n1, a.partials + blockIdx.x);
+            }
+            if (flags & (XY_GRAD | XY_GRAD_PRE)) {
+                __shared__ double gtot[2];
+                block_sum<2, NT>(gacc, gtot);
+                __syncthreads();
+                if (t == 0) {
+                    a.gd.acc[2 * blockIdx.x] += a.gd.coef * gtot[0];
+                    a.gd.acc[2 * blockIdx.x + 1] += a.gd.coef * gtot[1];
+                }
             }
         }
     }

@@ -114,6 +114,21 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
         __syncthreads();
     }
 
+    // adjoint gradient partial of one point: Im(conj(v) psi) g(y) D_j(z, x)
+    double gacc[2] = {0.0, 0.0};
+    auto grad_point = [&](const Cx<T> &v, int x, int y) {
+        const Cx<T> q = static_cast<const Cx<T> *>(a.gd.psi)[pbase + ((long long)y << g.lgnx) + x];
+        const double im = ((double)v.x * q.y - (double)v.y * q.x) * a.gd.g64[y];
+        gacc[0] += im * a.gd.D1[(long long)z * g.nx + x];
+        gacc[1] += im * a.gd.D3[(long long)z * g.nx + x];
+    };
+    if (flags & XY_GRAD_PRE) {
+        for (int e = threadIdx.x; e < E; e += kNT) {
+            const int j = e >> g.lgnx, x = e & (g.nx - 1);
+            grad_point(sm[j * g.pitchXY + x], x, r + j * g.P);
+        }
+    }
+
     if (flags & XY_IN_MIXED) {
         axis_inv<MAXV, kNT, T>(sm, LineMap{g.lgLy, 0, g.pitchXY, 1}, g.lgLy, g.apx, a.tw);
         axis_inv<MAXV, kNT, T>(sm, LineMap{g.lgnx, 0, 1, g.pitchXY}, g.lgnx, g.apy, a.tw);
@@ -128,11 +143,21 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
             if (flags & XY_RED_NORM) nacc[0] += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
             if (flags & XY_STATE_OUT)
                 a.state_out[pbase + ((long long)y << g.lgnx) + x] = v;
+            if (flags & XY_GRAD) grad_point(v, x, y);
             if (flags & XY_KICK_SPLIT) kick_point<T>(v, a.k, g, x, y, z, false);
             sm[j * g.pitchXY + x] = v;
         }
         if (flags & XY_RED_NORM) block_sum_store<1>(nacc, a.partials + blockIdx.x);
         __syncthreads();
+    }
+    if (flags & (XY_GRAD | XY_GRAD_PRE)) {
+        __shared__ double gtot[2];
+        block_sum_store<2>(gacc, gtot);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            a.gd.acc[2 * blockIdx.x] += a.gd.coef * gtot[0];
+            a.gd.acc[2 * blockIdx.x + 1] += a.gd.coef * gtot[1];
+        }
     }
 
     if (flags & XY_OUT_MIXED) {
@@ -323,29 +348,6 @@ __global__ void mask_kernel(const Cx<T> *psi, Cx<T> *lam, const Geom g, const do
     block_sum_store<1>(acc, partials + blockIdx.x);
 }
 
-template <class T>
-__global__ void grad_kernel(const Cx<T> *lam, const Cx<T> *psi, const Geom g, const double *g64,
-                            const double *D1, const double *D3, double c, double *R1, double *R3)
-{
-    const int z = blockIdx.x;
-    const long long base = (long long)z * g.plane;
-    double acc[2] = {0.0, 0.0};
-    for (int e = threadIdx.x; e < (int)g.plane; e += kNT) {
-        const int x = e & (g.nx - 1), y = e >> g.lgnx;
-        const Cx<T> l = lam[base + e], p = psi[base + e];
-        const double im = ((double)l.x * (double)p.y - (double)l.y * (double)p.x) * g64[y];
-        acc[0] += im * D1[(long long)z * g.nx + x];
-        acc[1] += im * D3[(long long)z * g.nx + x];
-    }
-    __shared__ double tot[2];
-    block_sum_store<2>(acc, tot);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        R1[z] += c * tot[0];
-        R3[z] += c * tot[1];
-    }
-}
-
 // -------------------------------------------------------------- launchers
 int xy_grid(const Geom &g) { return g.nz * g.P; }
 int z_grid(const Geom &g) { return g.Ly << g.nblk_lg; }
@@ -408,13 +410,6 @@ void launch_mask(const Cx<T> *psi, Cx<T> *lam, const Geom &g, const double *xcj,
     mask_kernel<T><<<nblk, kNT, 0, st>>>(psi, lam, g, xcj, hw, partials, chunk);
 }
 
-template <class T>
-void launch_grad(const Cx<T> *lam, const Cx<T> *psi, const Geom &g, const double *g64,
-                 const double *D1, const double *D3, double c, double *R1, double *R3,
-                 cudaStream_t st)
-{
-    grad_kernel<T><<<g.nz, kNT, 0, st>>>(lam, psi, g, g64, D1, D3, c, R1, R3);
-}
 
 template void launch_xy<float>(const XYArgs<float> &, cudaStream_t);
 template void launch_xy<double>(const XYArgs<double> &, cudaStream_t);
@@ -426,11 +421,5 @@ template void launch_mask<float>(const Cx<float> *, Cx<float> *, const Geom &, c
                                  double, double *, int, cudaStream_t);
 template void launch_mask<double>(const Cx<double> *, Cx<double> *, const Geom &, const double *,
                                   double, double *, int, cudaStream_t);
-template void launch_grad<float>(const Cx<float> *, const Cx<float> *, const Geom &,
-                                 const double *, const double *, const double *, double, double *,
-                                 double *, cudaStream_t);
-template void launch_grad<double>(const Cx<double> *, const Cx<double> *, const Geom &,
-                                  const double *, const double *, const double *, double,
-                                  double *, double *, cudaStream_t);
 
 }  // namespace ctap

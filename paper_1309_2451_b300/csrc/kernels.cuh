@@ -35,7 +35,20 @@ enum XYFlags {
     XY_KICK_SPLIT = 16,   // two factors of dt/2 with a reduction/state copy between
     XY_RED_NORM = 32,     // FP64 sum |psi|^2 after the first factor (imaginary time)
     XY_RED_OBS = 64,      // FP64 observables of the natural-layout input
-    XY_STATE_OUT = 128    // copy the state between the two half factors out
+    XY_STATE_OUT = 128,   // copy the state between the two half factors out
+    XY_GRAD_PRE = 256,    // adjoint: gradient partials on the input (before any kick)
+    XY_GRAD = 512         // adjoint: gradient partials after the first kick
+};
+
+// Adjoint gradient partials of one XY launch: for the state lambda held by
+// the pass and the forward state psi (natural layout), per CTA
+//   acc[cta][j] += coef * sum Im(conj(lambda) psi) g(y) D_j(z, x),  j = 1, 3.
+struct GradData {
+    const void *psi;          // forward state psi_m, natural layout
+    const double *g64;        // [ny]
+    const double *D1, *D3;    // [nz][nx]
+    double *acc;              // [xy_grid][2]
+    double coef;              // dt * w_m * dV
 };
 
 struct Geom {
@@ -86,6 +99,7 @@ template <class T> struct XYArgs {
     double *partials;         // per-CTA reduction results
     int flags;
     int small_angle;          // |V| dt <= 0.5 everywhere: no half-turn reduction
+    GradData gd;
 };
 
 template <class T> struct ZArgs {
@@ -120,10 +134,6 @@ template <class T> void launch_scale(Cx<T> *psi, long long n, const double *scal
 template <class T> void launch_mask(const Cx<T> *psi, Cx<T> *lam, const Geom &g,
                                     const double *xcj, double hw, double *partials,
                                     int nblk, cudaStream_t st);
-// R_j[z] += c * sum_{x,y} Im(conj(lam) psi) g(y) D_j(z,x), j = 1, 3.
-template <class T> void launch_grad(const Cx<T> *lam, const Cx<T> *psi, const Geom &g,
-                                    const double *g64, const double *D1, const double *D3,
-                                    double c, double *R1, double *R3, cudaStream_t st);
 int mask_blocks(const Geom &g);
 
 // fast_passes.cu: specialised passes (same layout as the generic ones); the
