@@ -229,6 +229,48 @@ def time_e2e(ctap, wl, torch, steps, device, stream, plan):
                 d2h_bytes_per_step=6 * 8)
 
 
+def time_cufft(torch, device, stream, plan, steps=20):
+    """Comparison step in the paper's own design (Sec. IV): a library 3D FFT
+    (torch.fft, i.e. cuFFT) and separate elementwise phase multiplies, on the
+    same complex64 workload, half-kicks merged as in the fused path.  Not the
+    product path: it only puts the fused two-pass step in context."""
+    nz, ny, nx = SHAPE
+    N = nz * ny * nx
+    box = plan.box
+    V = torch.from_numpy(plan.get_potential()).to(device)
+    k = [2.0 * np.pi * np.fft.fftfreq(n, d=(box[2 * a + 1] - box[2 * a]) / n)
+         for a, n in ((2, nz), (1, ny), (0, nx))]
+    kz, ky, kx = (torch.from_numpy(v).to(device) for v in k)
+    k2h = 0.5 * (kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2)
+    PK = (torch.exp(-1j * k2h * DT) / N).to(torch.complex64)
+    PV = torch.exp(-1j * V * DT).to(torch.complex64)
+    del V, k2h
+    dims = (0, 1, 2)
+
+    def one(psi):
+        psi = torch.fft.fftn(psi, dim=dims, norm="backward")
+        psi.mul_(PK)
+        psi = torch.fft.ifftn(psi, dim=dims, norm="forward")
+        return psi.mul_(PV)
+
+    with torch.cuda.stream(stream):
+        psi = torch.randn(SHAPE, dtype=torch.complex64, device=device)
+        for _ in range(3):
+            psi = one(psi)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            psi = one(psi)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    del PK, PV, psi
+    torch.cuda.empty_cache()
+    return {"steps_per_s": 1000.0 / ms, "ms_per_step": ms, "steps": steps,
+            "design": "torch.fft (cuFFT) 3D C2C forward + inverse and two elementwise "
+                      "phase multiplies per step, complex64, merged half-kicks"}
+
+
 def time_rows(ctap, wl, torch, device, stream):
     """The hot-path rows outside the headline loop, each timed once with CUDA
     events: imaginary-time preparation of the guide-1 transverse state
@@ -401,6 +443,7 @@ def run_ours(a):
         del r64
     if rank == 0 and not a.no_extras:
         extra["rows"] = time_rows(ctap, wl, torch, device, stream)
+        extra["cufft_comparison"] = time_cufft(torch, device, stream, res["plan"])
         extra["cpu_baseline"] = cpu_baseline()
     e2e = time_e2e(ctap, wl, torch, max(3, a.steps // 4), device, stream, res["plan"])
     if world > 1:
