@@ -246,6 +246,7 @@ template <class T> ZArgs<T> z_args(PlanState &st, const TabSet *ts, int imag)
     a.inv_n = (T)(1.0 / (double)st.N);
     a.k2h = st.d_k2h;
     a.partials = st.d_partials;
+    a.ring = st.no_ring ? 0 : 1;
     return a;
 }
 
@@ -756,6 +757,8 @@ ctap_status ctap_plan_create(int nx, int ny, int nz, const double *box, ctap_dty
     const int emax = kNT * maxv;
     const char *fg = std::getenv("CTAP_FORCE_GENERIC");
     st.force_generic = fg && fg[0] == '1';
+    const char *nr = std::getenv("CTAP_NO_RING");
+    st.no_ring = nr && nr[0] == '1';
     try {
         build_geometry(st, emax, maxv);
     } catch (const std::exception &) {

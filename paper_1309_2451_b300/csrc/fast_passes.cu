@@ -33,6 +33,9 @@
 //   Tile columns are XOR-swizzled per z (column ^ W (z mod 16/W)) so that
 //   the z-major accesses of Z1/Z5 and the column accesses of Z2-Z4 are both
 //   free of bank conflicts.
+#include <algorithm>
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace ctap {
@@ -229,10 +232,13 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
     const C2 *src = a.src + pbase;
     C2 *dst = a.dst + pbase;
     // x and y twiddles staged in shared memory (after the tile)
-    Lift<T> *wx = reinterpret_cast<Lift<T> *>(sm + LY * PITCH);   // exp(-2 pi i e/NX)
+    // wx[rr RA + j] = exp(-2 pi i j rr/NX) (j < RA, rr < RB): the twiddles of
+    // the last x stage in the order the 16 lanes of a row read them (one
+    // table row per rr: consecutive lanes, consecutive entries, no conflicts)
+    Lift<T> *wx = reinterpret_cast<Lift<T> *>(sm + LY * PITCH);
     Lift<T> *wy = wx + NX;                                            // exp(-2 pi i e/LY)
     for (int e = t; e < NX + LY; e += NT)
-        wx[e] = e < NX ? a.tw[g.fast_x_off + e] : a.tw[g.fast_y_off + e - NX];
+        wx[e] = e < NX ? a.tw[g.fast_x_off + (e % RA) * (e / RA)] : a.tw[g.fast_y_off + e - NX];
     const int flags = HOT ? XY_KICK_FULL : a.flags;
     const Kick<T> &k = a.k;
     const bool kick = (flags & (XY_KICK_HALF | XY_KICK_FULL | XY_KICK_SPLIT)) != 0;
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
                     const int j = q % RA, row = q / RA;
                     dft_inv<RB, 0, 1, T>(v[i]);
 #pragma unroll
-                    for (int rr = 1; rr < RB; ++rr) lift_b<T>(v[i][rr], wx[j * rr]);
+                    for (int rr = 1; rr < RB; ++rr) lift_b<T>(v[i][rr], wx[rr * RA + j]);
 #pragma unroll
                     for (int rr = 0; rr < RB; ++rr) sm[row * PITCH + j + RA * rr] = v[i][rr];
                 }
@@ -527,7 +533,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) v[rr] = sm[row * PITCH + j + RA * rr];
 #pragma unroll
-            for (int rr = 1; rr < RB; ++rr) lift_f<T>(v[rr], wx[j * rr]);
+            for (int rr = 1; rr < RB; ++rr) lift_f<T>(v[rr], wx[rr * RA + j]);
             dft_fwd<RB, 0, 1, T>(v);
             C2 *rowp = dst + ((long long)(row * g.P + r) << g.lgnx);
             sfor<RB>([&](auto kc) {
@@ -782,8 +788,258 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
     }
 }
 
+// =================================================================== Z ring
+// Persistent form of the complex64 Z pass for 1024-point lines and 16-column
+// tiles (P = 4 row classes, W = 4 columns): one CTA per SM walks over tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The tile lives in a ring of
+// twelve 128-row chunks of shared memory (a tile is eight chunks).  While a
+// tile is transformed, 16-byte asynchronous copies (cp.async, no registers
+// held) bring in the first half of the next tile; its second half follows as
+// soon as the store phase has drained the current tile's first half.  The
+// HBM load latency of a tile is thereby hidden behind the previous tile's
+// shared-memory phases instead of stalling the SM.
+//
+// Phases per tile: Z1 cross twiddle + P-point DFT in place, Z2-Z4 as in
+// z_fast_kernel, Z5 inverse cross DFT and streaming stores.  Same arithmetic
+// and HBM layout as z_fast_kernel.
+namespace {
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kRingCHZ = 128;            // z-rows per ring chunk
+
+}  // namespace
+
+template <int NZ, int ZA, int ZB, int P, int W>
+__global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, int ntiles)
+{
+    static_assert(ZA * ZB == NZ && ZA == 32 && ZB == 32, "1024-point lines as 32 x 32");
+    static_assert(P * W == 16 && W == 4, "16-column tiles of 32-byte row segments");
+    using T = float;
+    using C2 = float2;
+    constexpr int NT = 256;
+    constexpr int C = P * W;
+    constexpr int CHZ = kRingCHZ;
+    constexpr int NCH = NZ / CHZ;                  // chunks per tile (8)
+    constexpr int NRING = NCH + NCH / 2;           // ring slots (12)
+    constexpr int CHE = CHZ * C;                   // complex values per chunk
+    constexpr int SWM = 16 / W - 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2 *ring = reinterpret_cast<C2 *>(smraw);
+    Lift<T> *wz = reinterpret_cast<Lift<T> *>(ring + NRING * CHE);
+    Lift<T> *kz = wz + NZ;
+    const Geom &g = a.g;
+    const int t = threadIdx.x;
+    const int G = gridDim.x;
+    const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
+    const int nblk_mask = (1 << g.nblk_lg) - 1;
+    const Lift<T> *wc = a.tw + g.cross_off;
+
+    // ring slot of chunk c of the i-th tile of this CTA
+    auto slot_of = [](int i, int c) {
+        int s = (i % 3) * 8 + c;           // 8 i mod 12 = 0, 8, 4 for i mod 3 = 0, 1, 2
+        s -= (s >= NRING) ? NRING : 0;
+        s -= (s >= NRING) ? NRING : 0;
+        return s;
+    };
+    // asynchronous copy of chunks [c0, c1) of the i-th tile into the ring
+    auto issue = [&](int i, int c0, int c1) {
+        const int tile = blockIdx.x + i * G;
+        const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
+        const C2 *base = a.src + ((long long)(kp * P) << g.lgnx) + b * W;
+        const int n = (c1 - c0) * CHZ * P * 2;
+        for (int e = t; e < n; e += NT) {
+            const int h = e & 1, r = (e >> 1) & (P - 1);
+            const int zz = c0 * CHZ + (e >> 3);
+            const C2 *src = base + (long long)zz * g.plane + ((long long)r << g.lgnx) + 2 * h;
+            C2 *dst = ring + slot_of(i, zz / CHZ) * CHE + (zz % CHZ) * C +
+                      ((r * W + 2 * h) ^ ((zz & SWM) * W));
+            cp_async16(dst, src);
+        }
+    };
+
+    if (nmine > 0) issue(0, 0, NCH);
+    cp_async_commit();
+    for (int e = t; e < NZ; e += NT) {
+        wz[e] = a.tw[g.fast_z_off + e];
+        kz[e] = a.kin[g.nx + g.ny + e];
+    }
+    const T sc = a.inv_n * (a.scale ? (T)(*a.scale) : T(1));
+
+    for (int i = 0; i < nmine; ++i) {
+        const int tile = blockIdx.x + i * G;
+        const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
+        if (i + 1 < nmine) issue(i + 1, 0, NCH / 2);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();                         // tile i (and the tables) visible
+
+        int sb[NCH];                             // ring offset of each chunk of tile i
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) sb[c] = slot_of(i, c) * CHE;
+        auto at = [&](int zz, int col) {
+            int s = slot_of(i, zz / CHZ);
+            return s * CHE + (zz % CHZ) * C + (col ^ ((zz & SWM) * W));
+        };
+        Lift<T> cw[P];
+#pragma unroll
+        for (int rr = 1; rr < P; ++rr) cw[rr] = wc[(rr * kp) & (g.ny - 1)];
+        const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
+
+        // Z1: cross twiddle + forward P-point DFT, in place (two columns per task)
+        for (int q = t; q < NZ * (W / 2); q += NT) {
+            const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
+            C2 v[2][P];
+#pragma unroll
+            for (int rr = 0; rr < P; ++rr) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(ring + at(zz, rr * W + xo));
+                v[0][rr] = make_float2(w4.x, w4.y);
+                v[1][rr] = make_float2(w4.z, w4.w);
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                for (int rr = 1; rr < P; ++rr) lift_f<T>(v[c][rr], cw[rr]);
+                dft_fwd<P, 0, 1, T>(v[c]);
+            }
+            sfor<P>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                const C2 e0 = v[0][brev(k2, P)], e1 = v[1][brev(k2, P)];
+                *reinterpret_cast<float4 *>(ring + at(zz, k2 * W + xo)) = make_float4(e0.x, e0.y, e1.x, e1.y);
+            });
+        }
+        __syncthreads();
+
+        // Z2: forward z, first stage (radix ZA) on rows j + ZB rr, in place.
+        // Row j + ZB rr lies in chunk rr / 4 (ZB = 32, 128-row chunks).
+        for (int q = t; q < C * ZB; q += NT) {
+            const int col = q % C, j = q / C;
+            const int off = j * C + (col ^ ((j & SWM) * W));
+            C2 v[ZA];
+#pragma unroll
+            for (int rr = 0; rr < ZA; ++rr) v[rr] = ring[sb[rr / 4] + (rr % 4) * ZB * C + off];
+            dft_fwd<ZA, 0, 1, T>(v);
+            sfor<ZA>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                ring[sb[kk / 4] + (kk % 4) * ZB * C + off] = v[brev(kk, ZA)];
+            });
+        }
+        __syncthreads();
+
+        // Z3: last stage on the contiguous rows ZB jp + j, kinetic factor, inverse
+        for (int q = t; q < C * ZA; q += NT) {
+            const int col = q % C, jp = q / C;
+            const int kx = b * W + (col % W);
+            const int ky = kp + ((col / W) << g.lgLy);
+            const int rowbase = slot_of(i, (ZB * jp) / CHZ) * CHE + ((ZB * jp) % CHZ) * C;
+            C2 v[ZB];
+#pragma unroll
+            for (int j = 0; j < ZB; ++j) v[j] = ring[rowbase + j * C + (col ^ ((j & SWM) * W))];
+            sfor<ZB - 1>([&](auto jc) {
+                constexpr int j = decltype(jc)::value + 1;
+                if constexpr (j % 4 == 0) hoist_fence();
+                lift_f<T>(v[j], wz[jp * j]);
+            });
+            dft_fwd<ZB, 0, 1, T>(v);
+            const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky];
+            sfor<ZB>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                if constexpr (k2 % 4 == 0) hoist_fence();
+                C2 &u = v[brev(k2, ZB)];
+                const Lift<T> az = kz[jp + ZA * k2];
+                if (a.imag) {
+                    const T f = ax.f * ay.f * az.f * sc;
+                    u.x *= f;
+                    u.y *= f;
+                } else {
+                    rot_f<T>(u, ax.p, ax.u);
+                    rot_f<T>(u, ay.p, ay.u);
+                    rot_f<T>(u, az.p, az.u);
+                    const T s = ax.s * ay.s * az.s * sc;
+                    u.x *= s;
+                    u.y *= s;
+                }
+            });
+            dft_inv<ZB, 0, 1, T>(v);
+            sfor<ZB - 1>([&](auto jc) {
+                constexpr int j = decltype(jc)::value + 1;
+                if constexpr (j % 4 == 0) hoist_fence();
+                lift_b<T>(v[j], wz[jp * j]);
+            });
+#pragma unroll
+            for (int j = 0; j < ZB; ++j) ring[rowbase + j * C + (col ^ ((j & SWM) * W))] = v[j];
+        }
+        __syncthreads();
+
+        // Z4: inverse z, first stage, in place
+        for (int q = t; q < C * ZB; q += NT) {
+            const int col = q % C, j = q / C;
+            const int off = j * C + (col ^ ((j & SWM) * W));
+            C2 v[ZA];
+            sfor<ZA>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                v[brev(kk, ZA)] = ring[sb[kk / 4] + (kk % 4) * ZB * C + off];
+            });
+            dft_inv<ZA, 0, 1, T>(v);
+#pragma unroll
+            for (int rr = 0; rr < ZA; ++rr) ring[sb[rr / 4] + (rr % 4) * ZB * C + off] = v[rr];
+        }
+        __syncthreads();
+
+        // Z5: inverse cross DFT and store; once the first half of the tile is
+        // out, its chunks receive the second half of the next tile
+        auto z5 = [&](int q0, int q1) {
+            for (int q = q0 + t; q < q1; q += NT) {
+                const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
+                C2 v[2][P];
+                sfor<P>([&](auto kc) {
+                    constexpr int k2 = decltype(kc)::value;
+                    const float4 w4 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + xo));
+                    v[0][brev(k2, P)] = make_float2(w4.x, w4.y);
+                    v[1][brev(k2, P)] = make_float2(w4.z, w4.w);
+                });
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    dft_inv<P, 0, 1, T>(v[c]);
+#pragma unroll
+                    for (int rr = 1; rr < P; ++rr) lift_b<T>(v[c][rr], cw[rr]);
+                }
+                C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
+#pragma unroll
+                for (int rr = 0; rr < P; ++rr)
+                    __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
+                           make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y));
+            }
+        };
+        z5(0, NZ * (W / 2) / 2);
+        __syncthreads();
+        if (i + 1 < nmine) issue(i + 1, NCH / 2, NCH);
+        cp_async_commit();
+        z5(NZ * (W / 2) / 2, NZ * (W / 2));
+        __syncthreads();                         // tile i's chunks are free
+    }
+    cp_async_wait<0>();
+}
+
 // ================================================================ dispatch
 namespace {
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
 
 template <class T, int NX, int RA, int RB, int LY, int YA, int YB>
 bool try_xy(const XYArgs<T> &a, cudaStream_t st)
@@ -831,6 +1087,23 @@ bool try_z(const ZArgs<T> &a, cudaStream_t st)
         cudaFuncSetAttribute(z_fast_kernel<T, NZ, ZA, ZB, P, W>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cfg = true;
+    }
+    if constexpr (std::is_same<T, float>::value && NZ == 1024 && P == 4 && W == 4) {
+        if (a.ring && !a.observe && a.src == a.dst) {
+            constexpr int NRING = 12;
+            const size_t rsmem = (size_t)NRING * kRingCHZ * P * W * sizeof(Cx<T>) +
+                                 2 * NZ * sizeof(Lift<T>);
+            static bool rcfg = false;
+            if (!rcfg) {
+                cudaFuncSetAttribute(z_ring_kernel<NZ, ZA, ZB, P, W>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+                rcfg = true;
+            }
+            const int ntiles = z_grid(a.g);
+            const int grid = std::min(ntiles, sm_count());
+            z_ring_kernel<NZ, ZA, ZB, P, W><<<grid, 256, rsmem, st>>>(a, ntiles);
+            return true;
+        }
     }
     z_fast_kernel<T, NZ, ZA, ZB, P, W><<<z_grid(a.g), z_threads<T>(NZ), smem, st>>>(a);
     return true;

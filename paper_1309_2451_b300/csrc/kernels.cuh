@@ -114,6 +114,7 @@ template <class T> struct ZArgs {
     const double *k2h;        // for the kinetic-energy reduction
     double *partials;
     int observe;              // 1: forward only, reduce sum k^2/2 |psi_k|^2, no store
+    int ring;                 // 1: the persistent ring form may be used (in place only)
 };
 
 template <class T> void launch_xy(const XYArgs<T> &a, cudaStream_t st);

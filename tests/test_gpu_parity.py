@@ -356,6 +356,30 @@ def test_fast_and_generic_passes_match_oracle(ctap, shape, monkeypatch):
     assert np.allclose(obs_f, obs_g, rtol=1e-6, atol=1e-9)
 
 
+def test_persistent_z_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
+    """The persistent Z pass (shared-memory ring refilled by asynchronous
+    copies while the previous tile is transformed) is used for 1024-point
+    z-lines with 4 row classes; it must agree with the one-tile-per-CTA Z pass
+    and with the oracle."""
+    shape, box = (1024, 256, 64), wl.CTAP_BOX
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=15) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    info = plan.info()
+    assert info["fast_mask"] == 3 and info["row_classes"] == 4 and info["cols_per_z_tile"] == 16
+    psi = to_dev(psi0, "c64")
+    plan.step(psi, 2, 0.0025)
+    ring = psi.cpu().numpy().astype(complex)
+    monkeypatch.setenv("CTAP_NO_RING", "1")
+    pplan, _, _ = guides_plan(ctap, shape, box, "c64")
+    psi = to_dev(psi0, "c64")
+    pplan.step(psi, 2, 0.0025)
+    plain = psi.cpu().numpy().astype(complex)
+    assert rel(ring, plain) < 1e-6
+    ref = oracle.step(psi0, V, box, 0.0025, 2)
+    assert rel(ring, ref) < 1e-6
+
+
 FAST128_SHAPES = [(256, 128, 128), (256, 256, 256), (512, 256, 256), (1024, 128, 256),
                   (64, 64, 64), (16, 32, 128)]
 
