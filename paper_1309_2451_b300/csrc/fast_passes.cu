@@ -851,23 +851,45 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
         s -= (s >= NRING) ? NRING : 0;
         return s;
     };
-    // asynchronous copy of chunks [c0, c1) of the i-th tile into the ring
+    // asynchronous copy of chunks [c0, c1) of the i-th tile into the ring.
+    // Thread t always moves the same 16-byte piece (half h of row class r)
+    // of z-rows t/8 + 32 m, so its addresses advance by fixed strides.
+    const int ch = t & 1, cr = (t >> 1) & (P - 1), czl = t >> 3;
+    const int cdst = czl * C + ((cr * W + 2 * ch) ^ ((czl & SWM) * W));
     auto issue = [&](int i, int c0, int c1) {
         const int tile = blockIdx.x + i * G;
         const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
-        const C2 *base = a.src + ((long long)(kp * P) << g.lgnx) + b * W;
-        const int n = (c1 - c0) * CHZ * P * 2;
-        for (int e = t; e < n; e += NT) {
-            const int h = e & 1, r = (e >> 1) & (P - 1);
-            const int zz = c0 * CHZ + (e >> 3);
-            const C2 *src = base + (long long)zz * g.plane + ((long long)r << g.lgnx) + 2 * h;
-            C2 *dst = ring + slot_of(i, zz / CHZ) * CHE + (zz % CHZ) * C +
-                      ((r * W + 2 * h) ^ ((zz & SWM) * W));
-            cp_async16(dst, src);
+        const C2 *src = a.src + ((long long)(kp * P + cr) << g.lgnx) + b * W + 2 * ch +
+                        (long long)(c0 * CHZ + czl) * g.plane;
+        const long long zstep = (long long)(NT / 8) * g.plane;
+        for (int c = c0; c < c1; ++c) {
+            C2 *dst = ring + slot_of(i, c) * CHE + cdst;
+#pragma unroll
+            for (int m = 0; m < CHZ / (NT / 8); ++m) {
+                cp_async16(dst + m * (NT / 8) * C, src);
+                src += zstep;
+            }
+        }
+    };
+    // per-tile tables, double buffered: kinetic x factors of the W columns,
+    // kinetic y factors of the P classes, cross twiddles
+    __shared__ Lift<T> tabs[2][W + 2 * P];
+    auto load_tabs = [&](int i) {
+        if (t < W + 2 * P) {
+            const int tile = blockIdx.x + i * G;
+            const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
+            Lift<T> v;
+            if (t < W) v = a.kin[b * W + t];
+            else if (t < W + P) v = a.kin[g.nx + kp + ((t - W) << g.lgLy)];
+            else v = wc[((t - W - P) * kp) & (g.ny - 1)];
+            tabs[i & 1][t] = v;
         }
     };
 
-    if (nmine > 0) issue(0, 0, NCH);
+    if (nmine > 0) {
+        issue(0, 0, NCH);
+        load_tabs(0);
+    }
     cp_async_commit();
     for (int e = t; e < NZ; e += NT) {
         wz[e] = a.tw[g.fast_z_off + e];
@@ -878,10 +900,14 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
     for (int i = 0; i < nmine; ++i) {
         const int tile = blockIdx.x + i * G;
         const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
-        if (i + 1 < nmine) issue(i + 1, 0, NCH / 2);
+        if (i + 1 < nmine) {
+            issue(i + 1, 0, NCH / 2);
+            load_tabs(i + 1);
+        }
         cp_async_commit();
         cp_async_wait<1>();
-        __syncthreads();                         // tile i (and the tables) visible
+        __syncthreads();                         // tile i (and its tables) visible
+        const Lift<T> *tb = tabs[i & 1];
 
         int sb[NCH];                             // ring offset of each chunk of tile i
 #pragma unroll
@@ -890,9 +916,6 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
             int s = slot_of(i, zz / CHZ);
             return s * CHE + (zz % CHZ) * C + (col ^ ((zz & SWM) * W));
         };
-        Lift<T> cw[P];
-#pragma unroll
-        for (int rr = 1; rr < P; ++rr) cw[rr] = wc[(rr * kp) & (g.ny - 1)];
         const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
 
         // Z1: cross twiddle + forward P-point DFT, in place (two columns per task)
@@ -908,7 +931,7 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
 #pragma unroll
-                for (int rr = 1; rr < P; ++rr) lift_f<T>(v[c][rr], cw[rr]);
+                for (int rr = 1; rr < P; ++rr) lift_f<T>(v[c][rr], tb[W + P + rr]);
                 dft_fwd<P, 0, 1, T>(v[c]);
             }
             sfor<P>([&](auto kc) {
@@ -938,8 +961,6 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
         // Z3: last stage on the contiguous rows ZB jp + j, kinetic factor, inverse
         for (int q = t; q < C * ZA; q += NT) {
             const int col = q % C, jp = q / C;
-            const int kx = b * W + (col % W);
-            const int ky = kp + ((col / W) << g.lgLy);
             const int rowbase = slot_of(i, (ZB * jp) / CHZ) * CHE + ((ZB * jp) % CHZ) * C;
             C2 v[ZB];
 #pragma unroll
@@ -950,7 +971,7 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
                 lift_f<T>(v[j], wz[jp * j]);
             });
             dft_fwd<ZB, 0, 1, T>(v);
-            const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky];
+            const Lift<T> ax = tb[col % W], ay = tb[W + col / W];
             sfor<ZB>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
                 if constexpr (k2 % 4 == 0) hoist_fence();
@@ -995,36 +1016,36 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
         }
         __syncthreads();
 
-        // Z5: inverse cross DFT and store; once the first half of the tile is
-        // out, its chunks receive the second half of the next tile
-        auto z5 = [&](int q0, int q1) {
-            for (int q = q0 + t; q < q1; q += NT) {
-                const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
-                C2 v[2][P];
-                sfor<P>([&](auto kc) {
-                    constexpr int k2 = decltype(kc)::value;
-                    const float4 w4 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + xo));
-                    v[0][brev(k2, P)] = make_float2(w4.x, w4.y);
-                    v[1][brev(k2, P)] = make_float2(w4.z, w4.w);
-                });
+        // Z5: inverse cross DFT and store, one chunk (128 z-rows) per round;
+        // as soon as chunk m < NCH/2 is drained, chunk NCH/2 + m of the next
+        // tile is copied into its slot
+        for (int m = 0; m < NCH; ++m) {
+            const int q = m * CHZ * (W / 2) + t;
+            const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
+            C2 v[2][P];
+            sfor<P>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                const float4 w4 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + xo));
+                v[0][brev(k2, P)] = make_float2(w4.x, w4.y);
+                v[1][brev(k2, P)] = make_float2(w4.z, w4.w);
+            });
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    dft_inv<P, 0, 1, T>(v[c]);
+            for (int c = 0; c < 2; ++c) {
+                dft_inv<P, 0, 1, T>(v[c]);
 #pragma unroll
-                    for (int rr = 1; rr < P; ++rr) lift_b<T>(v[c][rr], cw[rr]);
-                }
-                C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
-#pragma unroll
-                for (int rr = 0; rr < P; ++rr)
-                    __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
-                           make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y));
+                for (int rr = 1; rr < P; ++rr) lift_b<T>(v[c][rr], tb[W + P + rr]);
             }
-        };
-        z5(0, NZ * (W / 2) / 2);
-        __syncthreads();
-        if (i + 1 < nmine) issue(i + 1, NCH / 2, NCH);
-        cp_async_commit();
-        z5(NZ * (W / 2) / 2, NZ * (W / 2));
+            C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
+#pragma unroll
+            for (int rr = 0; rr < P; ++rr)
+                __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
+                       make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y));
+            if (m < NCH / 2) {
+                __syncthreads();                 // chunk m drained by every thread
+                if (i + 1 < nmine) issue(i + 1, NCH / 2 + m, NCH / 2 + m + 1);
+                cp_async_commit();
+            }
+        }
         __syncthreads();                         // tile i's chunks are free
     }
     cp_async_wait<0>();
