@@ -208,16 +208,21 @@ template <int NQ, int NT = kFastNT> __device__ void block_sum(double (&acc)[NQ],
 // ======================================================================= XY
 // HOT: the steady real-time step with the product potential (full kick, no
 // reductions, small angles) compiled without per-point flag tests.
-// threads per XY CTA: 512 for complex64, 256 for complex128 (register budget)
-template <class T> __host__ __device__ constexpr int xy_threads() { return sizeof(T) == 4 ? 512 : 256; }
+// threads per XY CTA (register budget): the hot complex64 variant fits in 64
+// registers and runs 1024 threads (32 warps hide more shared-memory and
+// HBM latency); the other complex64 variants 512, complex128 256
+template <class T, bool HOT = false> __host__ __device__ constexpr int xy_threads()
+{
+    return sizeof(T) == 4 ? (HOT ? 1024 : 512) : 256;
+}
 
 template <class T, int NX, int RA, int RB, int LY, int YA, int YB, bool IN_MIXED, bool OUT_MIXED,
           bool HOT>
-__global__ void __launch_bounds__(xy_threads<T>()) xy_fast_kernel(const XYArgs<T> a)
+__global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYArgs<T> a)
 {
     static_assert(RA * RB == NX && YA * YB == LY, "radix split");
     using C2 = Cx<T>;
-    constexpr int NT = xy_threads<T>();
+    constexpr int NT = xy_threads<T, HOT>();
     constexpr int PITCH = NX + 2;          // even: rows stay 16-byte aligned
     extern __shared__ __align__(16) unsigned char smraw[];
     C2 *sm = reinterpret_cast<C2 *>(smraw);
@@ -788,20 +793,7 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
     }
 }
 
-// =================================================================== Z ring
-// Persistent form of the complex64 Z pass for 1024-point lines and 16-column
-// tiles (P = 4 row classes, W = 4 columns): one CTA per SM walks over tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...  The tile lives in a ring of
-// twelve 128-row chunks of shared memory (a tile is eight chunks).  While a
-// tile is transformed, 16-byte asynchronous copies (cp.async, no registers
-// held) bring in the first half of the next tile; its second half follows as
-// soon as the store phase has drained the current tile's first half.  The
-// HBM load latency of a tile is thereby hidden behind the previous tile's
-// shared-memory phases instead of stalling the SM.
-//
-// Phases per tile: Z1 cross twiddle + P-point DFT in place, Z2-Z4 as in
-// z_fast_kernel, Z5 inverse cross DFT and streaming stores.  Same arithmetic
-// and HBM layout as z_fast_kernel.
+// ------------------------------------------------ asynchronous copies
 namespace {
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
@@ -818,6 +810,21 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
 constexpr int kRingCHZ = 128;            // z-rows per ring chunk
 
 }  // namespace
+
+// =================================================================== Z ring
+// Persistent form of the complex64 Z pass for 1024-point lines and 16-column
+// tiles (P = 4 row classes, W = 4 columns): one CTA per SM walks over tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The tile lives in a ring of
+// twelve 128-row chunks of shared memory (a tile is eight chunks).  While a
+// tile is transformed, 16-byte asynchronous copies (cp.async, no registers
+// held) bring in the first half of the next tile; its second half follows as
+// soon as the store phase has drained the current tile's first half.  The
+// HBM load latency of a tile is thereby hidden behind the previous tile's
+// shared-memory phases instead of stalling the SM.
+//
+// Phases per tile: Z1 cross twiddle + P-point DFT in place, Z2-Z4 as in
+// z_fast_kernel, Z5 inverse cross DFT and streaming stores.  Same arithmetic
+// and HBM layout as z_fast_kernel.
 
 template <int NZ, int ZA, int ZB, int P, int W>
 __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, int ntiles)
@@ -1084,7 +1091,7 @@ bool try_xy(const XYArgs<T> &a, cudaStream_t st)
     const bool hot = a.flags == (XY_IN_MIXED | XY_OUT_MIXED | XY_KICK_FULL) &&
                      a.k.form == VF_PRODUCT && !a.k.imag && a.small_angle;
     if (hot)
-        xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, true><<<grid, NT, smem, st>>>(a);
+        xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, true><<<grid, xy_threads<T, true>(), smem, st>>>(a);
     else if (in && out)
         xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, false><<<grid, NT, smem, st>>>(a);
     else if (in)

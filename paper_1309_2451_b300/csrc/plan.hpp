@@ -48,7 +48,7 @@ struct PlanState {
     Geom geom;
     int timeout_ms = 60000;
     bool force_generic = false;    // CTAP_FORCE_GENERIC=1 at plan creation
-    bool no_ring = false;          // CTAP_NO_RING=1: non-persistent Z pass only
+    bool no_ring = false;          // CTAP_NO_RING=1: one-tile-per-CTA Z pass only
     bool fast_xy = false, fast_z = false;
     double vmax = 0.0;             // max |V| over the grid (small-angle kick test)
 
