@@ -46,7 +46,10 @@ extern "C" {
 typedef struct ctap_plan *ctap_plan_t;          /* opaque, library-owned */
 
 typedef enum { CTAP_C64 = 0, CTAP_C128 = 1 } ctap_dtype;
-typedef enum { CTAP_REAL = 0, CTAP_IMAG = 1 } ctap_time;
+/* Time stepping of ctap_step: real time in the symmetric order V/2 K V/2
+ * (the default), imaginary time in the same order, or real time in the
+ * order K/2 V K/2 (the alternative Strang ordering). */
+typedef enum { CTAP_REAL = 0, CTAP_IMAG = 1, CTAP_REAL_KVK = 2 } ctap_time;
 
 typedef enum {
     CTAP_OK = 0,
@@ -105,6 +108,18 @@ ctap_status ctap_set_guides_spline(ctap_plan_t plan, double V0, double s, int nk
                                    const double *knots_z, const double *c12,
                                    const double *c23, double halfwidth, int set_regions);
 
+/* Add a z-only term Vz(z) (host FP64 [nz]) to the potential the plan holds,
+ * e.g. the longitudinal harmonic trap of Sec. III that drives the atom along
+ * the guides and refocuses it at the far turning point.  For the product
+ * form the term is kept separately (V = g(y) H(x,z) + Vz(z): one extra phase
+ * per z-plane, no extra memory traffic); for the dense and separable forms it
+ * is folded into the stored potential.  Calls accumulate; any ctap_set_*
+ * call replaces the whole potential including this term.  The adjoint
+ * gradient is unaffected (Vz does not depend on the guide controls).
+ * Errors: CTAP_ERR_NO_POTENTIAL before a potential is set,
+ * CTAP_ERR_INVALID_ARG for a null pointer or a non-finite value. */
+ctap_status ctap_add_potential_z(ctap_plan_t plan, const double *Vz);
+
 /* Copy the potential the plan holds, evaluated in FP64 on the grid, into V
  * (host, [nz][ny][nx]).  For checking the potential builders. */
 ctap_status ctap_get_potential(ctap_plan_t plan, double *V);
@@ -112,7 +127,11 @@ ctap_status ctap_get_potential(ctap_plan_t plan, double *V);
 /* Advance psi (device, in place) by nsteps Strang steps of size dt.
  * mode CTAP_REAL: exp(-i V dt/2), exp(-i |k|^2 dt/2); CTAP_IMAG: real
  * factors exp(-V dt/2), exp(-|k|^2 dt/2) and renormalisation to
- * sum |psi|^2 dV = 1 after every step (Sec. V ground-state preparation).
+ * sum |psi|^2 dV = 1 after every step (Sec. V ground-state preparation);
+ * CTAP_REAL_KVK: real time with the kinetic factor split instead,
+ * exp(-i |k|^2 dt/4) exp(-i V dt) exp(-i |k|^2 dt/4) per step (the
+ * ordering of Sec. IV's four transforms per step; consecutive kinetic
+ * halves merge, so it costs the same two passes per step).
  * Asynchronous on the plan stream.  nsteps == 0 is a no-op. */
 ctap_status ctap_step(ctap_plan_t plan, void *psi, int nsteps, double dt, ctap_time mode);
 
@@ -134,6 +153,11 @@ ctap_status ctap_observables(ctap_plan_t plan, const void *psi, double *out);
  * dJ/dc12, grad[m..2m-1] = dJ/dc23 (m = nknots).  Synchronises. */
 ctap_status ctap_adjoint(ctap_plan_t plan, const void *psi0, int nsteps, double dt,
                          int K, int guide, double *J, double *grad);
+
+/* Density integrated over y (Sec. V, Fig. 5): out[z][x] = sum_y |psi|^2 dy,
+ * FP64 accumulated in a fixed order, psi device (not modified), out host
+ * [nz][nx].  Synchronises. */
+ctap_status ctap_density_xz(ctap_plan_t plan, const void *psi, double *out);
 
 /* Wait for the plan's stream; CTAP_ERR_TIMEOUT after timeout_ms
  * (timeout_ms <= 0: the plan's default, see ctap_set_timeout). */

@@ -39,6 +39,8 @@ def _load():
         lib.orc_fft3d.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_step.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        lib.orc_step_kvk.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                     ctypes.c_double, ctypes.c_int]
         lib.orc_observables.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         _dp, _dp, ctypes.c_double, _dp]
         lib.orc_ctap_potential.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
@@ -119,21 +121,39 @@ def fft3d(psi, direction):
 
 # --------------------------------------------------------------- split step
 
-def step(psi, V, box, dt, nsteps, imag=False):
-    """nsteps Strang split steps (V/2, K, V/2) of size dt; returns a new array.
+def step(psi, V, box, dt, nsteps, imag=False, order="VKV"):
+    """nsteps Strang split steps of size dt; returns a new array.
 
-    Sec. IV: Fourier split-operator method.  imag=True is the imaginary-time
-    variant (real factors exp(-V dt/2), exp(-k^2 dt/2)) with renormalisation
-    to sum |psi|^2 dV = 1 after every step (Sec. V obtains the transverse
-    ground state numerically)."""
+    Sec. IV: Fourier split-operator method.  order "VKV" is V/2, K, V/2;
+    order "KVK" is K/2, V, K/2 (real time only).  imag=True is the
+    imaginary-time variant (real factors exp(-V dt/2), exp(-k^2 dt/2)) with
+    renormalisation to sum |psi|^2 dV = 1 after every step (Sec. V obtains the
+    transverse ground state numerically)."""
     out = _c128(psi).copy()
     nz, ny, nx = out.shape
     Vd = _f64(V)
     if Vd.shape != out.shape:
         raise ValueError("V must have the shape of psi")
+    if order == "KVK":
+        if imag:
+            raise ValueError("the K/2 V K/2 ordering is real time only")
+        _check(_load().orc_step_kvk(_ptr(out.view(np.float64)), _ptr(Vd), nx, ny, nz,
+                                    _ptr(_box(box)), float(dt), int(nsteps)), "step_kvk")
+        return out
+    if order != "VKV":
+        raise ValueError("order must be 'VKV' or 'KVK'")
     _check(_load().orc_step(_ptr(out.view(np.float64)), _ptr(Vd), nx, ny, nz, _ptr(_box(box)),
                             float(dt), int(nsteps), 1 if imag else 0), "step")
     return out
+
+
+def density_xz(psi, box):
+    """Density integrated over y, n(z, x) = sum_y |psi|^2 dy, in FP64: the
+    quantity Fig. 5 shows in the x-z plane (Sec. V)."""
+    a = _c128(psi)
+    ny = a.shape[1]
+    dy = (box[3] - box[2]) / ny
+    return (a.real ** 2 + a.imag ** 2).sum(axis=1) * dy
 
 
 def observables(psi, V, box, centres=None, halfwidth=1.5):

@@ -235,6 +235,30 @@ int orc_step(double *psi, const double *V, int nx, int ny, int nz,
     return 0;
 }
 
+/* nsteps real-time steps of the other Strang ordering, K/2 V K/2 (the
+ * kinetic factor split, the potential factor whole): per step
+ * psihat = F psi; psihat *= exp(-i |k|^2 dt/4); psi = F^-1 psihat;
+ * psi *= exp(-i V dt); psihat = F psi; psihat *= exp(-i |k|^2 dt/4);
+ * psi = F^-1 psihat.  Sec. IV counts four transforms per step, which is this
+ * ordering applied literally.  Nothing is merged across steps. */
+int orc_step_kvk(double *psi, const double *V, int nx, int ny, int nz,
+                 const double *box, double dt, int nsteps)
+{
+    if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nsteps < 0) return -1;
+    cplx *a = (cplx *)psi;
+    long N = (long)nx * ny * nz;
+    for (int s = 0; s < nsteps; ++s) {
+        orc_fft3d(psi, nx, ny, nz, -1);
+        kinetic_factor(a, nx, ny, nz, box, 0.5 * dt, 0);
+        orc_fft3d(psi, nx, ny, nz, +1);
+        potential_factor(a, V, N, dt, 0);
+        orc_fft3d(psi, nx, ny, nz, -1);
+        kinetic_factor(a, nx, ny, nz, box, 0.5 * dt, 0);
+        orc_fft3d(psi, nx, ny, nz, +1);
+    }
+    return 0;
+}
+
 /* --------------------------------------------------------- observables */
 
 /* out[0] = sum |psi|^2 dV                       (norm)

@@ -216,6 +216,7 @@ template <class T> XYArgs<T> xy_args(PlanState &st, const TabSet *ts, double dt,
     a.k.Vd = reinterpret_cast<const T *>(st.d_Vd);
     a.k.g = reinterpret_cast<const T *>(st.d_g);
     a.k.H = reinterpret_cast<const T *>(st.d_H);
+    a.k.vz = reinterpret_cast<const T *>(st.d_vz);
     if (ts && ts->sep) {
         const size_t n = (size_t)(st.nx + st.ny + st.nz);
         a.k.sep_half = reinterpret_cast<const Lift<T> *>(ts->sep);
@@ -226,6 +227,7 @@ template <class T> XYArgs<T> xy_args(PlanState &st, const TabSet *ts, double dt,
     a.rd.Vsep = st.d_vsep64;
     a.rd.g64 = st.d_g64;
     a.rd.H64 = st.d_H64;
+    a.rd.vz64 = st.d_vz64;
     a.rd.xc = st.have_regions ? st.d_xc : nullptr;
     a.rd.hw = st.hw;
     a.rd.k2h = st.d_k2h;
@@ -287,10 +289,39 @@ template <class F> ctap_status go_other(PlanState &st, const char *what, F f)
     return post_launch(st, what);
 }
 
-// nsteps Strang steps on psi (device, natural layout in and out)
-template <class T> ctap_status run_steps(PlanState &st, Cx<T> *psi, int n, double dt, int imag)
+// K/2 V K/2 steps in real time: the kinetic halves of consecutive steps
+// merge, so the pass sequence is XY (forward only), Z (K/2), n times
+// [XY (inverse, full V, forward), Z (K, the last one K/2)], XY (inverse only).
+template <class T> ctap_status run_steps_kvk(PlanState &st, Cx<T> *psi, int n, double dt)
+{
+    TabSet *ts = nullptr;
+    CTAP_TRY(get_tables(st, dt, 0, &ts));
+    XYArgs<T> xa = xy_args<T>(st, ts, dt, 0);
+    ZArgs<T> za = z_args<T>(st, ts, 0);         // kinetic pointers copied before the
+    TabSet *th = nullptr;                       // cache may move its entries
+    CTAP_TRY(get_tables(st, 0.5 * dt, 0, &th));
+    ZArgs<T> zh = z_args<T>(st, th, 0);
+    xa.src = za.src = zh.src = psi;
+    xa.dst = za.dst = zh.dst = psi;
+    xa.flags = XY_OUT_MIXED;
+    CTAP_TRY(go_xy<T>(st, xa));
+    CTAP_TRY(go_z<T>(st, zh));
+    for (int s = 0; s < n; ++s) {
+        xa.flags = XY_IN_MIXED | XY_KICK_FULL | XY_OUT_MIXED;
+        CTAP_TRY(go_xy<T>(st, xa));
+        CTAP_TRY(go_z<T>(st, s + 1 < n ? za : zh));
+    }
+    xa.flags = XY_IN_MIXED;
+    return go_xy<T>(st, xa);
+}
+
+// nsteps Strang steps on psi (device, natural layout in and out); mode is a
+// ctap_time value
+template <class T> ctap_status run_steps(PlanState &st, Cx<T> *psi, int n, double dt, int mode)
 {
     if (n <= 0) return CTAP_OK;
+    if (mode == CTAP_REAL_KVK) return run_steps_kvk<T>(st, psi, n, dt);
+    const int imag = mode == CTAP_IMAG ? 1 : 0;
     TabSet *ts = nullptr;
     CTAP_TRY(get_tables(st, dt, imag, &ts));
     XYArgs<T> xa = xy_args<T>(st, ts, dt, imag);
@@ -334,8 +365,9 @@ template <class T> ctap_status run_steps(PlanState &st, Cx<T> *psi, int n, doubl
 // call runs eagerly; the second captures the launch sequence once (tables are
 // uploaded before capture begins) and replays it; later calls replay.
 
-template <class T> ctap_status step_maybe_graph(PlanState &st, Cx<T> *psi, int n, double dt, int imag)
+template <class T> ctap_status step_maybe_graph(PlanState &st, Cx<T> *psi, int n, double dt, int mode)
 {
+    const int imag = mode;                      // graph key: the full ctap_time mode
     const bool usable = st.graphs && st.stream != nullptr && !st.profiling &&
                         !std::getenv("CTAP_FAULT_INJECT") && n > 0;
     if (!usable) return run_steps<T>(st, psi, n, dt, imag);
@@ -347,9 +379,7 @@ template <class T> ctap_status step_maybe_graph(PlanState &st, Cx<T> *psi, int n
                 st.launches += g.launches;
                 return CTAP_OK;
             }
-            // second sighting: capture
-            TabSet *ts = nullptr;
-            CTAP_TRY(get_tables(st, dt, imag, &ts));
+            // second sighting: capture (tables are built by the eager first call)
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamBeginCapture(st.stream, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(st, e, "begin capture");
@@ -623,6 +653,9 @@ void clear_potential(PlanState &st)
     dev_free_t(st.d_g64);
     dev_free_t(st.d_H64);
     dev_free_t(st.d_vsep64);
+    dev_free(st.d_vz);
+    dev_free_t(st.d_vz64);
+    st.h_vz.clear();
     st.h_V.clear();
     st.h_vsep.clear();
     st.h_g.clear();
@@ -804,6 +837,7 @@ ctap_status ctap_plan_destroy(ctap_plan_t plan)
     dev_free_t(st.d_D3);
     dev_free_t(st.d_partials);
     dev_free_t(st.d_red);
+    dev_free_t(st.d_dens);
     for (auto &e : st.events) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -901,6 +935,68 @@ ctap_status ctap_set_guides_spline(ctap_plan_t plan, double V0, double s, int nk
     return CTAP_OK;
 }
 
+ctap_status ctap_add_potential_z(ctap_plan_t plan, const double *Vz)
+{
+    PlanState *st = S(plan);
+    if (!st || !Vz) return CTAP_ERR_INVALID_ARG;
+    if (st->vform == VF_NONE) return CTAP_ERR_NO_POTENTIAL;
+    const int nx = st->nx, ny = st->ny, nz = st->nz;
+    double vzmax = 0.0;
+    for (int z = 0; z < nz; ++z) {
+        if (!std::isfinite(Vz[z])) return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite potential");
+    }
+    drop_graphs(*st);
+    if (st->vform == VF_DENSE) {
+        for (int z = 0; z < nz; ++z)
+            for (size_t i = 0; i < (size_t)nx * ny; ++i) st->h_V[(size_t)z * nx * ny + i] += Vz[z];
+        CTAP_TRY(upload_prec(*st, &st->d_Vd, st->h_V));
+        st->vmax = 0.0;
+        for (double v : st->h_V) st->vmax = std::max(st->vmax, std::fabs(v));
+    } else if (st->vform == VF_SEPARABLE) {
+        for (int z = 0; z < nz; ++z) st->h_vsep[(size_t)nx + ny + z] += Vz[z];
+        CTAP_TRY(upload64(*st, &st->d_vsep64, st->h_vsep));
+        invalidate_sep(*st);
+    } else {
+        if (st->h_vz.empty()) st->h_vz.assign(nz, 0.0);
+        for (int z = 0; z < nz; ++z) {
+            st->h_vz[z] += Vz[z];
+            vzmax = std::max(vzmax, std::fabs(st->h_vz[z]));
+        }
+        CTAP_TRY(upload_prec(*st, &st->d_vz, st->h_vz));
+        CTAP_TRY(upload64(*st, &st->d_vz64, st->h_vz));
+        double gm = 0.0, hm = 0.0;
+        for (double v : st->h_g) gm = std::max(gm, std::fabs(v));
+        for (double v : st->h_H) hm = std::max(hm, std::fabs(v));
+        st->vmax = gm * hm + vzmax;
+    }
+    return CTAP_OK;
+}
+
+ctap_status ctap_density_xz(ctap_plan_t plan, const void *psi, double *out)
+{
+    PlanState *st = S(plan);
+    if (!st || !psi || !out) return CTAP_ERR_INVALID_ARG;
+    const size_t n = (size_t)st->nz * st->nx;
+    if (!st->d_dens) {
+        void *q = nullptr;
+        CTAP_TRY(dev_alloc(*st, &q, n * sizeof(double)));
+        st->d_dens = static_cast<double *>(q);
+    }
+    const double dy = (st->box[3] - st->box[2]) / st->ny;
+    CTAP_TRY(go_other(*st, "density", [&] {
+        if (st->dtype == CTAP_C64)
+            launch_density_xz<float>(static_cast<const float2 *>(psi), st->geom, dy, st->d_dens,
+                                     st->stream);
+        else
+            launch_density_xz<double>(static_cast<const double2 *>(psi), st->geom, dy, st->d_dens,
+                                      st->stream);
+    }));
+    cudaError_t e = cudaMemcpyAsync(out, st->d_dens, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    st->stream);
+    if (e != cudaSuccess) return cuda_fail(*st, e, "density copy");
+    return wait_stream(*st, 0);
+}
+
 ctap_status ctap_get_potential(ctap_plan_t plan, double *V)
 {
     PlanState *st = S(plan);
@@ -915,7 +1011,8 @@ ctap_status ctap_get_potential(ctap_plan_t plan, double *V)
                 if (st->vform == VF_DENSE) v = st->h_V[i];
                 else if (st->vform == VF_SEPARABLE)
                     v = st->h_vsep[x] + st->h_vsep[nx + y] + st->h_vsep[nx + ny + z];
-                else v = st->h_g[y] * st->h_H[(size_t)z * nx + x];
+                else v = st->h_g[y] * st->h_H[(size_t)z * nx + x] +
+                         (st->h_vz.empty() ? 0.0 : st->h_vz[z]);
                 V[i] = v;
             }
     return CTAP_OK;
@@ -925,13 +1022,12 @@ ctap_status ctap_step(ctap_plan_t plan, void *psi, int nsteps, double dt, ctap_t
 {
     PlanState *st = S(plan);
     if (!st || !psi || nsteps < 0 || !std::isfinite(dt)) return CTAP_ERR_INVALID_ARG;
-    if (mode != CTAP_REAL && mode != CTAP_IMAG) return CTAP_ERR_INVALID_ARG;
+    if (mode != CTAP_REAL && mode != CTAP_IMAG && mode != CTAP_REAL_KVK) return CTAP_ERR_INVALID_ARG;
     if (st->vform == VF_NONE) return CTAP_ERR_NO_POTENTIAL;
     if (reinterpret_cast<uintptr_t>(psi) % st->esize) return fail(*st, CTAP_ERR_INVALID_ARG, "psi misaligned");
-    const int imag = mode == CTAP_IMAG;
     if (st->dtype == CTAP_C64)
-        return step_maybe_graph<float>(*st, static_cast<float2 *>(psi), nsteps, dt, imag);
-    return step_maybe_graph<double>(*st, static_cast<double2 *>(psi), nsteps, dt, imag);
+        return step_maybe_graph<float>(*st, static_cast<float2 *>(psi), nsteps, dt, (int)mode);
+    return step_maybe_graph<double>(*st, static_cast<double2 *>(psi), nsteps, dt, (int)mode);
 }
 
 ctap_status ctap_observables(ctap_plan_t plan, const void *psi, double *out)

@@ -249,6 +249,8 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
     const bool kick = (flags & (XY_KICK_HALF | XY_KICK_FULL | XY_KICK_SPLIT)) != 0;
     const bool full = (flags & XY_KICK_FULL) != 0;
     const T tau = full ? k.tau_full : k.tau_half;
+    // additive z-only term of the product form: one phase for the whole plane
+    const T thz = k.vz ? k.vz[z] * tau : T(0);
 
     auto swx = [](int x) { return RA * (x % RB) + x / RB; };     // natural x -> position
     auto unswx = [](int p) { return p / RA + RB * (p % RA); };   // position -> natural x
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                     }
                     const double hz =
                         (a.vform_obs == VF_PRODUCT) ? a.rd.H64[(long long)z * g.nx + x] : 0.0;
+                    const double vz64 = a.rd.vz64 ? a.rd.vz64[z] : 0.0;
                     const double vxz = (a.vform_obs == VF_SEPARABLE)
                                            ? a.rd.Vsep[x] + a.rd.Vsep[g.nx + g.ny + z] : 0.0;
 #pragma unroll
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                         const double d = (double)u.x * u.x + (double)u.y * u.y;
                         double V = 0.0;
                         if (a.vform_obs == VF_DENSE) V = (double)k.Vd[pbase + ((long long)y << g.lgnx) + x];
-                        else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * hz;
+                        else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * hz + vz64;
                         else if (a.vform_obs == VF_SEPARABLE) V = vxz + a.rd.Vsep[g.nx + y];
                         acc[0] += d;
                         acc[1] += V * d;
@@ -414,7 +417,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                 if (HOT) {
                     const T hx = htab[p];
 #pragma unroll
-                    for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], gtab[i + YB * rr] * hx, 1);
+                    for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], fmadd(gtab[i + YB * rr], hx, thz), 1);
                     // (the hot variant is only chosen when the short series applies)
                 } else if (kick) {
                     if (k.form == VF_SEPARABLE) {
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                             const int jy = i + YB * rr;
                             const T th =
                                 (k.form == VF_PRODUCT)
-                                    ? gtab[jy] * hx
+                                    ? fmadd(gtab[jy], hx, thz)
                                     : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
                             kick_one<T>(v[c][rr], th, k.imag, small);
                             if (flags & XY_RED_NORM)
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                             for (int rr = 0; rr < YA; ++rr) {
                                 const int jy = i + YB * rr;
                                 const T th = (k.form == VF_PRODUCT)
-                                                 ? gtab[jy] * hx
+                                                 ? fmadd(gtab[jy], hx, thz)
                                                  : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
                                 kick_one<T>(v[c][rr], th, k.imag, small);
                             }

@@ -56,7 +56,8 @@ __device__ __forceinline__ void kick_point(Cx<T> &v, const Kick<T> &k, const Geo
         }
     } else {
         const T V = (k.form == VF_DENSE) ? k.Vd[((long long)z * g.ny + y) * g.nx + x]
-                                         : k.g[y] * k.H[(long long)z * g.nx + x];
+                                         : k.g[y] * k.H[(long long)z * g.nx + x] +
+                                               (k.vz ? k.vz[z] : T(0));
         const T th = V * (full ? k.tau_full : k.tau_half);
         if (k.imag) {
             const T f = dexp(-th);
@@ -98,7 +99,8 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
             const double d = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
             double V = 0.0;
             if (a.vform_obs == VF_DENSE) V = (double)a.k.Vd[(pbase + ((long long)y << g.lgnx)) + x];
-            else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * a.rd.H64[(long long)z * g.nx + x];
+            else if (a.vform_obs == VF_PRODUCT)
+                V = a.rd.g64[y] * a.rd.H64[(long long)z * g.nx + x] + (a.rd.vz64 ? a.rd.vz64[z] : 0.0);
             else if (a.vform_obs == VF_SEPARABLE)
                 V = a.rd.Vsep[x] + a.rd.Vsep[g.nx + y] + a.rd.Vsep[g.nx + g.ny + z];
             acc[0] += d;
@@ -348,6 +350,23 @@ __global__ void mask_kernel(const Cx<T> *psi, Cx<T> *lam, const Geom g, const do
     block_sum_store<1>(acc, partials + blockIdx.x);
 }
 
+// ------------------------------------------------- y-integrated density
+// One thread per (z, x): sum over y in ascending order (deterministic).
+template <class T>
+__global__ void density_xz_kernel(const Cx<T> *psi, const Geom g, double dy, double *out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)g.nz * g.nx) return;
+    const int z = (int)(i >> g.lgnx), x = (int)(i & (g.nx - 1));
+    const Cx<T> *p = psi + (long long)z * g.plane + x;
+    double acc = 0.0;
+    for (int y = 0; y < g.ny; ++y) {
+        const Cx<T> v = p[(long long)y << g.lgnx];
+        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+    out[i] = acc * dy;
+}
+
 // -------------------------------------------------------------- launchers
 int xy_grid(const Geom &g) { return g.nz * g.P; }
 int z_grid(const Geom &g) { return g.Ly << g.nblk_lg; }
@@ -411,6 +430,15 @@ void launch_mask(const Cx<T> *psi, Cx<T> *lam, const Geom &g, const double *xcj,
 }
 
 
+template <class T>
+void launch_density_xz(const Cx<T> *psi, const Geom &g, double dy, double *out, cudaStream_t st)
+{
+    const long long n = (long long)g.nz * g.nx;
+    density_xz_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, g, dy, out);
+}
+
+template void launch_density_xz<float>(const Cx<float> *, const Geom &, double, double *, cudaStream_t);
+template void launch_density_xz<double>(const Cx<double> *, const Geom &, double, double *, cudaStream_t);
 template void launch_xy<float>(const XYArgs<float> &, cudaStream_t);
 template void launch_xy<double>(const XYArgs<double> &, cudaStream_t);
 template void launch_z<float>(const ZArgs<float> &, cudaStream_t);

@@ -74,6 +74,7 @@ template <class T> struct Kick {
     const T *H;               // product, [nz][nx]
     const Lift<T> *sep_half;  // separable, [nx | ny | nz] for tau = dt/2
     const Lift<T> *sep_full;  // separable, tau = dt
+    const T *vz;              // product form: additive z-only term Vz(z) [nz], or null
     T tau_half, tau_full;
 };
 
@@ -82,6 +83,7 @@ struct RedData {
     const double *Vsep;       // [nx | ny | nz] for separable V
     const double *g64;        // [ny]
     const double *H64;        // [nz][nx]
+    const double *vz64;       // product form: additive Vz(z) [nz], or null
     const double *xc;         // guide centres [3][nz] or null
     double hw;                // population half-width
     const double *k2h;        // k^2/2 per axis [nx | ny | nz]
@@ -136,6 +138,9 @@ template <class T> void launch_mask(const Cx<T> *psi, Cx<T> *lam, const Geom &g,
                                     const double *xcj, double hw, double *partials,
                                     int nblk, cudaStream_t st);
 int mask_blocks(const Geom &g);
+// out[z][x] = dy sum_y |psi(z, y, x)|^2 (FP64, fixed summation order)
+template <class T> void launch_density_xz(const Cx<T> *psi, const Geom &g, double dy, double *out,
+                                          cudaStream_t st);
 
 // fast_passes.cu: specialised passes (same layout as the generic ones); the
 // launchers return false when the geometry is not covered.  esize is the

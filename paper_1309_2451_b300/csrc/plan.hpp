@@ -65,6 +65,9 @@ struct PlanState {
     void *d_Vd = nullptr;          // dense, plan precision
     void *d_g = nullptr;           // product g, plan precision
     void *d_H = nullptr;           // product H, plan precision
+    std::vector<double> h_vz;      // product form: additive Vz(z), empty if none
+    void *d_vz = nullptr;          // Vz, plan precision
+    double *d_vz64 = nullptr;      // Vz, FP64 (observables)
     double *d_g64 = nullptr, *d_H64 = nullptr, *d_vsep64 = nullptr;
 
     // guides (population regions and adjoint data)
@@ -86,6 +89,7 @@ struct PlanState {
     double *d_red = nullptr;       // 8 doubles
     double *d_scale = nullptr;     // 1 double
     void *d_work = nullptr;        // one psi, lazily (observables)
+    double *d_dens = nullptr;      // nz x nx doubles, lazily (density_xz)
 
     // accounting
     long long launches = 0;

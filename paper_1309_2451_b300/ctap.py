@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libctap.so")
 
 CTAP_C64, CTAP_C128 = 0, 1
-CTAP_REAL, CTAP_IMAG = 0, 1
+CTAP_REAL, CTAP_IMAG, CTAP_REAL_KVK = 0, 1, 2
 STATUS = ["ok", "invalid argument", "unsupported size", "dtype mismatch", "no potential",
           "out of memory", "CUDA error", "timeout", "non-finite result"]
 
@@ -48,6 +48,8 @@ def lib():
         "ctap_set_guides": [_vp, d, d, _dp, _dp, d, i],
         "ctap_set_guides_spline": [_vp, d, d, i, _dp, _dp, _dp, d, i],
         "ctap_get_potential": [_vp, _dp],
+        "ctap_add_potential_z": [_vp, _dp],
+        "ctap_density_xz": [_vp, _vp, _dp],
         "ctap_step": [_vp, _vp, i, d, i],
         "ctap_observables": [_vp, _vp, _dp],
         "ctap_adjoint": [_vp, _vp, i, d, i, i, _dp, _dp],
@@ -79,7 +81,8 @@ def exported_symbols():
             "ctap_set_guides_spline", "ctap_get_potential", "ctap_step", "ctap_observables",
             "ctap_adjoint", "ctap_sync", "ctap_set_timeout", "ctap_launch_count",
             "ctap_set_profiling", "ctap_pass_times", "ctap_plan_info", "ctap_status_string",
-            "ctap_last_error", "ctap_version", "ctap_norm_noalloc"]
+            "ctap_last_error", "ctap_version", "ctap_norm_noalloc", "ctap_add_potential_z",
+            "ctap_density_xz"]
 
 
 def _f64(a, n=None):
@@ -172,16 +175,34 @@ class Plan:
                                                  float(halfwidth), 1 if set_regions else 0))
         self.nknots = k.size
 
+    def add_potential_z(self, Vz):
+        """Add a z-only term Vz(z) (e.g. the longitudinal trap) to the potential."""
+        self._check(lib().ctap_add_potential_z(self._h, _p(_f64(Vz, self.shape[0]))))
+
     def get_potential(self):
         V = np.empty(self.shape)
         self._check(lib().ctap_get_potential(self._h, _p(V)))
         return V
 
     # ---------------------------------------------------------- propagation
-    def step(self, psi, nsteps, dt, imag=False):
-        self._check(lib().ctap_step(self._h, self._psi(psi), int(nsteps), float(dt),
-                                    CTAP_IMAG if imag else CTAP_REAL))
+    def step(self, psi, nsteps, dt, imag=False, order="VKV"):
+        """order "VKV" (V/2 K V/2) or "KVK" (K/2 V K/2, real time only)."""
+        if order == "KVK":
+            if imag:
+                raise ValueError("the K/2 V K/2 ordering is real time only")
+            mode = CTAP_REAL_KVK
+        elif order == "VKV":
+            mode = CTAP_IMAG if imag else CTAP_REAL
+        else:
+            raise ValueError("order must be 'VKV' or 'KVK'")
+        self._check(lib().ctap_step(self._h, self._psi(psi), int(nsteps), float(dt), mode))
         return psi
+
+    def density_xz(self, psi):
+        """sum_y |psi|^2 dy as an (nz, nx) FP64 array (Fig. 5)."""
+        out = np.zeros((self.shape[0], self.shape[2]))
+        self._check(lib().ctap_density_xz(self._h, self._psi(psi), _p(out)))
+        return out
 
     def observables(self, psi):
         out = np.zeros(6)

@@ -41,6 +41,10 @@ V0 = 20.0
 SIGMA_GUIDE = 1.0
 POP_HALFWIDTH = 1.5
 KNOTS_Z = tuple(-60.0 + 8.0 * m for m in range(16))
+# longitudinal trap: a packet released at rest at z = -40 reaches the far
+# turning point z = +40 after half a period pi/omega, with peak momentum
+# 40 omega = 3.2 (resolved by nz >= 256 on the 120-long box)
+TRAP_OMEGA = 0.08
 
 
 def axis(n, lo, hi):
@@ -72,10 +76,28 @@ def separation(z, zc, dmin=PROFILE["dmin"], dmax=PROFILE["dmax"], w=PROFILE["w"]
     return dmin + (dmax - dmin) * (1.0 - np.exp(-(z - zc) ** 2 / (2.0 * w * w)))
 
 
-def guide_centres(z):
-    """x_1(z) = -d12(z), x_2 = 0, x_3(z) = +d23(z) as a (3, nz) array."""
+def guide_centres(z, order="counter"):
+    """x_1(z) = -d12(z), x_2 = 0, x_3(z) = +d23(z) as a (3, nz) array.
+
+    order "counter": the middle-right pair approaches first (counter-intuitive
+    sequence, Fig. 4a); order "intuitive": the two profiles are exchanged, so
+    the left-middle pair approaches first (Fig. 4b)."""
     z = np.asarray(z, dtype=np.float64)
-    return np.stack([-separation(z, ZC_12), np.zeros_like(z), separation(z, ZC_23)])
+    if order == "counter":
+        zc12, zc23 = ZC_12, ZC_23
+    elif order == "intuitive":
+        zc12, zc23 = ZC_23, ZC_12
+    else:
+        raise ValueError("order must be 'counter' or 'intuitive'")
+    return np.stack([-separation(z, zc12), np.zeros_like(z), separation(z, zc23)])
+
+
+def trap_z(z, omega=TRAP_OMEGA, zc=0.0):
+    """Longitudinal harmonic trap omega^2 (z - zc)^2 / 2 centred on the chip
+    (Sec. III: it accelerates the atom along the guides and refocuses it at
+    the far turning point)."""
+    z = np.asarray(z, dtype=np.float64)
+    return 0.5 * omega * omega * (z - zc) ** 2
 
 
 def spline_controls():

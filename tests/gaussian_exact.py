@@ -54,6 +54,15 @@ class Gauss1D:
             self.kick(f * dt / 2.0)
         return self
 
+    def strang_ho_kvk(self, dt, nsteps):
+        """nsteps real-time steps of the other ordering for V = q^2/2:
+        drift dt/2, kick dt, drift dt/2."""
+        for _ in range(nsteps):
+            self.drift(dt / 2.0)
+            self.kick(dt)
+            self.drift(dt / 2.0)
+        return self
+
     def __call__(self, q):
         return np.exp(-self.A * q * q / 2.0 + self.B * q + self.C)
 

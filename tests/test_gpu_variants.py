@@ -1,0 +1,170 @@
+"""GPU parity of the paper-faithful variants against the FP64 oracle: the
+K/2 V K/2 ordering, the longitudinal harmonic trap (an additive z-only term,
+Sec. III), the intuitive guide arrangement (Fig. 4b) and the y-integrated
+density (Fig. 5).  Same tolerances as the main parity tests."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_2451_b300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctap():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_2451_b300 import build, ctap as c
+    build.build()
+    c.lib()
+    return c
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(psi, dtype):
+    t = torch.complex64 if dtype == "c64" else torch.complex128
+    return torch.from_numpy(np.ascontiguousarray(psi)).to(device="cuda", dtype=t)
+
+
+def guide_state(shape, box, seed):
+    return wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=seed) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+
+
+def guides(ctap, shape, box, dtype, order="counter", trap=None):
+    z = wl.axis(shape[0], box[4], box[5])
+    c = wl.guide_centres(z, order)
+    plan = ctap.Plan(shape, box, dtype)
+    plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    V = oracle.ctap_potential(shape, box, wl.V0, wl.SIGMA_GUIDE, c[0], c[2])
+    if trap is not None:
+        vz = wl.trap_z(z, trap)
+        plan.add_potential_z(vz)
+        V = V + vz[:, None, None]
+    return plan, V, c
+
+
+# fast-path shapes (specialised passes) and a generic one (ragged 8-point axes)
+SHAPES = [(256, 64, 64), (256, 128, 128), (64, 32, 16)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-6), ("c128", 1e-13)])
+def test_kvk_ordering_matches_oracle(ctap, shape, dtype, tol):
+    box = wl.CTAP_BOX
+    plan, V, _ = guides(ctap, shape, box, dtype)
+    psi0 = guide_state(shape, box, 21)
+    psi = to_dev(psi0, dtype)
+    plan.step(psi, 5, 0.02, order="KVK")
+    ref = oracle.step(psi0, V, box, 0.02, 5, order="KVK")
+    assert rel(psi.cpu().numpy().astype(complex), ref) < tol
+    # the orderings differ at this dt by far more than the tolerance
+    vkv = oracle.step(psi0, V, box, 0.02, 5)
+    assert rel(ref, vkv) > 10 * tol
+
+
+def test_kvk_graph_replay_matches_eager(ctap):
+    """Repeated KVK calls on a side stream are captured and replayed; the
+    capture is keyed on the ordering (a VKV call with the same arguments
+    must not reuse it)."""
+    shape, box = (256, 64, 64), wl.CTAP_BOX
+    side = torch.cuda.Stream()
+    z = wl.axis(shape[0], box[4], box[5])
+    c = wl.guide_centres(z)
+    psi0 = guide_state(shape, box, 22)
+    pg = ctap.Plan(shape, box, "c64", stream=side)
+    pg.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    pe = ctap.Plan(shape, box, "c64")
+    pe.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    a, b = to_dev(psi0, "c64"), to_dev(psi0, "c64")
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            pg.step(a, 4, 0.0025, order="KVK")
+        pg.step(a, 4, 0.0025)
+    for _ in range(3):
+        pe.step(b, 4, 0.0025, order="KVK")
+    pe.step(b, 4, 0.0025)
+    side.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(256, 64, 64), (64, 32, 16)])
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-6), ("c128", 1e-13)])
+def test_trap_term_matches_oracle(ctap, shape, dtype, tol):
+    """Guides plus the longitudinal trap, product form + z-only term, against
+    the oracle's dense V; observables (<V> includes the trap) too."""
+    box = wl.CTAP_BOX
+    plan, V, c = guides(ctap, shape, box, dtype, trap=wl.TRAP_OMEGA)
+    assert np.allclose(plan.get_potential(), V, rtol=1e-14, atol=1e-12)
+    psi0 = guide_state(shape, box, 23)
+    psi = to_dev(psi0, dtype)
+    plan.step(psi, 6, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, 6)
+    assert rel(psi.cpu().numpy().astype(complex), ref) < tol
+    got = plan.observables(psi)
+    want = oracle.observables(ref, V, box, c, wl.POP_HALFWIDTH)
+    assert np.allclose(got, want, rtol=1e-5 if dtype == "c64" else 1e-11, atol=1e-9)
+
+
+@pytest.mark.parametrize("form", ["dense", "separable"])
+def test_trap_term_on_dense_and_separable_forms(ctap, form):
+    shape, box = (32, 16, 16), (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
+    vx, vy, vz = wl.harmonic_parts(shape, box)
+    z = wl.axis(shape[0], box[4], box[5])
+    extra = 0.3 * np.sin(z)
+    plan = ctap.Plan(shape, box, "c128")
+    if form == "dense":
+        plan.set_potential(wl.harmonic_dense(shape, box))
+    else:
+        plan.set_potential_separable(vx, vy, vz)
+    plan.add_potential_z(extra)
+    V = wl.harmonic_dense(shape, box) + extra[:, None, None]
+    assert np.allclose(plan.get_potential(), V, rtol=1e-14, atol=1e-13)
+    psi0 = wl.gaussian_sum(shape, box, seed=24)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 10, 0.01)
+    assert rel(psi.cpu().numpy(), oracle.step(psi0, V, box, 0.01, 10)) < 1e-13
+
+
+def test_trap_requires_a_potential(ctap):
+    plan = ctap.Plan((8, 8, 8), (-1, 1, -1, 1, -1, 1), "c64")
+    with pytest.raises(ctap.CtapError) as e:
+        plan.add_potential_z(np.zeros(8))
+    assert e.value.code == 4
+    plan.set_potential(np.zeros((8, 8, 8)))
+    with pytest.raises(ctap.CtapError) as e:
+        plan.add_potential_z(np.full(8, np.nan))
+    assert e.value.code == 1
+
+
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-6), ("c128", 1e-13)])
+def test_intuitive_arrangement_matches_oracle(ctap, dtype, tol):
+    shape, box = (256, 64, 64), wl.CTAP_BOX
+    plan, V, c = guides(ctap, shape, box, dtype, order="intuitive")
+    psi0 = guide_state(shape, box, 25)
+    psi = to_dev(psi0, dtype)
+    plan.step(psi, 5, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, 5)
+    assert rel(psi.cpu().numpy().astype(complex), ref) < tol
+
+
+@pytest.mark.parametrize("shape", [(256, 64, 64), (1024, 256, 64), (8, 8, 8)])
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_density_xz_matches_oracle(ctap, shape, dtype):
+    box = wl.CTAP_BOX
+    psi0 = guide_state(shape, box, 26)
+    plan = ctap.Plan(shape, box, dtype)
+    psi = to_dev(psi0, dtype)
+    got = plan.density_xz(psi)
+    want = oracle.density_xz(psi.cpu().numpy().astype(complex), box)
+    assert got.shape == (shape[0], shape[2])
+    # FP64 accumulation of the stored values: only summation order differs
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-300)
+    # deterministic
+    assert np.array_equal(got, plan.density_xz(psi))
