@@ -229,6 +229,40 @@ def time_e2e(ctap, wl, torch, steps, device, stream, plan):
                 d2h_bytes_per_step=6 * 8)
 
 
+def time_variants(torch, wl, device, stream, plan, psi, reps=4):
+    """The paper-faithful variants on the bench workload, CUDA events on the
+    plan stream: the K/2 V K/2 ordering, the guides plus the longitudinal
+    trap term, and the y-integrated density of Fig. 5."""
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: plan.step(psi, SPLIT, DT, order="KVK"))
+    out["kvk_order"] = {"steps_per_s": SPLIT * 1000.0 / ms, "ms_per_step": ms / SPLIT}
+    z = wl.axis(SHAPE[0], wl.CTAP_BOX[4], wl.CTAP_BOX[5])
+    plan.add_potential_z(wl.trap_z(z))
+    ms = timed(lambda: plan.step(psi, SPLIT, DT))
+    out["guides_plus_trap"] = {"steps_per_s": SPLIT * 1000.0 / ms, "ms_per_step": ms / SPLIT}
+    c = wl.guide_centres(z)
+    plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)   # back to the bench V
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        plan.density_xz(psi)
+    out["density_xz"] = {"ms_per_call_with_copy": 1000.0 * (time.perf_counter() - t0) / reps,
+                         "bytes_read": int(np.prod(SHAPE)) * 8}
+    return out
+
+
 def time_cufft(torch, device, stream, plan, steps=20):
     """Comparison step in the paper's own design (Sec. IV): a library 3D FFT
     (torch.fft, i.e. cuFFT) and separate elementwise phase multiplies, on the
@@ -407,7 +441,7 @@ def run_ours(a):
     kind = 0 if pms[0] >= pms[1] else 1
     fast = res["plan"].info()["fast_mask"]
     name = (("xy_fast_kernel" if fast & 1 else "xy_pass_kernel") if kind == 0
-            else ("z_fast_kernel" if fast & 2 else "z_pass_kernel"))
+            else ("z_ring_kernel" if fast & 4 else ("z_fast_kernel" if fast & 2 else "z_pass_kernel")))
     avg_ms = pms[kind] / max(counts[kind], 1)
     bytes_launch = 2 * N * esize       # one read and one write of psi
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
@@ -443,6 +477,7 @@ def run_ours(a):
         del r64
     if rank == 0 and not a.no_extras:
         extra["rows"] = time_rows(ctap, wl, torch, device, stream)
+        extra["variants"] = time_variants(torch, wl, device, stream, res["plan"], res["psi"])
         extra["cufft_comparison"] = time_cufft(torch, device, stream, res["plan"])
         extra["cpu_baseline"] = cpu_baseline()
     e2e = time_e2e(ctap, wl, torch, max(3, a.steps // 4), device, stream, res["plan"])

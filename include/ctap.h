@@ -180,7 +180,9 @@ ctap_status ctap_pass_times(ctap_plan_t plan, long long counts[3], double ms[3])
 
 /* Pass geometry chosen for the plan: info[0] = P (row classes per plane),
  * info[1] = rows per XY tile, info[2] = columns per Z tile, info[3] = bytes
- * of one psi, info[4] = fast-pass mask (1: XY, 2: Z). */
+ * of one psi, info[4] = fast-pass mask (1: specialised XY pass, 2:
+ * specialised Z pass, 4: the in-place Z pass runs as the persistent ring
+ * kernel). */
 ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);
 
 /* Largest element count ctap_norm_noalloc accepts (2^27). */

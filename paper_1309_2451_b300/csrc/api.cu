@@ -1119,7 +1119,9 @@ ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5])
     info[1] = st->geom.Ly;
     info[2] = st->geom.C;
     info[3] = st->N * st->esize;
-    info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0);
+    const bool ring = st->fast_z && !st->no_ring && st->dtype == CTAP_C64 && st->nz == 1024 &&
+                      st->geom.P == 4 && st->geom.w == 4;
+    info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0) | (ring ? 4 : 0);
     return CTAP_OK;
 }
 

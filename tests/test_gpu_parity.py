@@ -366,12 +366,13 @@ def test_persistent_z_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
         * np.exp(2j * wl.mesh(shape, box)[2])
     plan, V, c = guides_plan(ctap, shape, box, "c64")
     info = plan.info()
-    assert info["fast_mask"] == 3 and info["row_classes"] == 4 and info["cols_per_z_tile"] == 16
+    assert info["fast_mask"] == 7 and info["row_classes"] == 4 and info["cols_per_z_tile"] == 16
     psi = to_dev(psi0, "c64")
     plan.step(psi, 2, 0.0025)
     ring = psi.cpu().numpy().astype(complex)
     monkeypatch.setenv("CTAP_NO_RING", "1")
     pplan, _, _ = guides_plan(ctap, shape, box, "c64")
+    assert pplan.info()["fast_mask"] == 3
     psi = to_dev(psi0, "c64")
     pplan.step(psi, 2, 0.0025)
     plain = psi.cpu().numpy().astype(complex)
