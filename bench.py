@@ -263,6 +263,55 @@ def time_variants(torch, wl, device, stream, plan, psi, reps=4):
     return out
 
 
+def time_batched(torch, wl, device, stream, B=10, shape=(256, 64, 128), steps=200):
+    """The parameter sweep of Fig. 6 as batched replicas: B middle-guide
+    depths on a small grid advanced by one batched plan, against the same B
+    runs one plan at a time (replica-steps per second)."""
+    box = wl.CTAP_BOX
+    z = wl.axis(shape[0], box[4], box[5])
+    c = wl.guide_centres(z)
+    mids = np.linspace(0.8, 1.2, B)
+    xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
+    one = wl.packet_from_transverse(wl.guide_seed_2d(shape[1:], box, xc), shape[0], box)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bp = ctap_mod().Plan(shape, box, "c64", stream=stream, batch=B)
+    bp.set_guides_batched(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], mids, wl.POP_HALFWIDTH)
+    psi = torch.from_numpy(np.stack([one] * B)).to(device, torch.complex64)
+    with torch.cuda.stream(stream):
+        bp.step(psi, steps, DT)
+        bp.step(psi, steps, DT)
+        e0.record(stream)
+        bp.step(psi, steps, DT)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    plans, psis = [], []
+    for m in mids:
+        p1 = ctap_mod().Plan(shape, box, "c64", stream=stream, batch=1)
+        p1.set_guides_batched(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], [m], wl.POP_HALFWIDTH)
+        plans.append(p1)
+        psis.append(torch.from_numpy(one).to(device, torch.complex64))
+    with torch.cuda.stream(stream):
+        for p1, q in zip(plans, psis):
+            p1.step(q, steps, DT)
+            p1.step(q, steps, DT)
+        e0.record(stream)
+        for p1, q in zip(plans, psis):
+            p1.step(q, steps, DT)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    return {"grid": list(shape[::-1]), "replicas": B, "steps": steps,
+            "batched_replica_steps_per_s": B * steps * 1000.0 / ms_b,
+            "sequential_replica_steps_per_s": B * steps * 1000.0 / ms_s,
+            "speedup": ms_s / ms_b}
+
+
+def ctap_mod():
+    from paper_1309_2451_b300 import ctap
+    return ctap
+
+
 def time_cufft(torch, device, stream, plan, steps=20):
     """Comparison step in the paper's own design (Sec. IV): a library 3D FFT
     (torch.fft, i.e. cuFFT) and separate elementwise phase multiplies, on the
@@ -478,6 +527,7 @@ def run_ours(a):
     if rank == 0 and not a.no_extras:
         extra["rows"] = time_rows(ctap, wl, torch, device, stream)
         extra["variants"] = time_variants(torch, wl, device, stream, res["plan"], res["psi"])
+        extra["variants"]["batched_sweep"] = time_batched(torch, wl, device, stream)
         extra["cufft_comparison"] = time_cufft(torch, device, stream, res["plan"])
         extra["cpu_baseline"] = cpu_baseline()
     e2e = time_e2e(ctap, wl, torch, max(3, a.steps // 4), device, stream, res["plan"])

@@ -70,6 +70,22 @@ typedef enum {
 ctap_status ctap_plan_create(int nx, int ny, int nz, const double *box,
                              ctap_dtype dtype, void *cuda_stream, ctap_plan_t *out);
 
+/* Batched replicas (the analogue of the paper's parameter sweep, Fig. 6):
+ * `batch` independent wave functions of the same grid in one psi buffer,
+ * [batch][nz][ny][nx], advanced together by every ctap_step launch (small
+ * grids fill the GPU).  Replicas differ only in their potential, which must
+ * be in product form (ctap_set_potential_product: the same for all;
+ * ctap_set_guides: the same for all; ctap_set_guides_batched: a middle-guide
+ * depth per replica); ctap_add_potential_z applies to every replica.
+ * ctap_observables returns 6 values per replica; ctap_density_xz and
+ * ctap_get_potential cover all replicas.  Real time only (CTAP_IMAG,
+ * ctap_set_guides_spline and ctap_adjoint need batch == 1 and return
+ * CTAP_ERR_INVALID_ARG otherwise).  batch in [1, CTAP_MAX_BATCH];
+ * ctap_plan_create is batch == 1. */
+#define CTAP_MAX_BATCH 1024
+ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const double *box,
+                                     ctap_dtype dtype, void *cuda_stream, ctap_plan_t *out);
+
 /* Free every device and host resource of the plan (waits for its stream).
  * Passing NULL returns CTAP_ERR_INVALID_ARG. */
 ctap_status ctap_plan_destroy(ctap_plan_t plan);
@@ -100,6 +116,14 @@ ctap_status ctap_set_guides(ctap_plan_t plan, double V0, double s,
                             const double *x1z, const double *x3z,
                             double halfwidth, int set_regions);
 
+/* The guides of ctap_set_guides with the middle guide's depth scaled per
+ * replica: replica b has V = -V0 (G_1 + mid_scale[b] G_2 + G_3) (the paper
+ * sweeps the middle-wire current I_M, Fig. 6).  mid_scale: host FP64
+ * [batch]. */
+ctap_status ctap_set_guides_batched(ctap_plan_t plan, double V0, double s, const double *x1z,
+                                    const double *x3z, const double *mid_scale,
+                                    double halfwidth, int set_regions);
+
 /* Same guides with x_1(z) = -d12(z), x_3(z) = +d23(z), where d12 and d23
  * are natural cubic splines through nknots knots (knots_z ascending, host)
  * with values c12[m], c23[m].  Required before ctap_adjoint.  nknots in
@@ -121,7 +145,7 @@ ctap_status ctap_set_guides_spline(ctap_plan_t plan, double V0, double s, int nk
 ctap_status ctap_add_potential_z(ctap_plan_t plan, const double *Vz);
 
 /* Copy the potential the plan holds, evaluated in FP64 on the grid, into V
- * (host, [nz][ny][nx]).  For checking the potential builders. */
+ * (host, [batch][nz][ny][nx]).  For checking the potential builders. */
 ctap_status ctap_get_potential(ctap_plan_t plan, double *V);
 
 /* Advance psi (device, in place) by nsteps Strang steps of size dt.
@@ -135,7 +159,8 @@ ctap_status ctap_get_potential(ctap_plan_t plan, double *V);
  * Asynchronous on the plan stream.  nsteps == 0 is a no-op. */
 ctap_status ctap_step(ctap_plan_t plan, void *psi, int nsteps, double dt, ctap_time mode);
 
-/* FP64-accumulated observables of psi (device, not modified), host out[6]:
+/* FP64-accumulated observables of psi (device, not modified), host out[6]
+ * (out[6 batch] for a batched plan, replica b at out + 6 b):
  *   out[0] = sum |psi|^2 dV                    (norm)
  *   out[1] = <T>, out[2] = <V>                  (normalised expectations)
  *   out[3..5] = population of guides 1..3: sum over |x - x_j(z)| < halfwidth
@@ -156,7 +181,7 @@ ctap_status ctap_adjoint(ctap_plan_t plan, const void *psi0, int nsteps, double 
 
 /* Density integrated over y (Sec. V, Fig. 5): out[z][x] = sum_y |psi|^2 dy,
  * FP64 accumulated in a fixed order, psi device (not modified), out host
- * [nz][nx].  Synchronises. */
+ * [batch][nz][nx].  Synchronises. */
 ctap_status ctap_density_xz(ctap_plan_t plan, const void *psi, double *out);
 
 /* Wait for the plan's stream; CTAP_ERR_TIMEOUT after timeout_ms

@@ -245,7 +245,7 @@ template <class T> ZArgs<T> z_args(PlanState &st, const TabSet *ts, int imag)
     a.tw = reinterpret_cast<const Lift<T> *>(st.d_tw);
     a.kin = ts ? reinterpret_cast<const Lift<T> *>(ts->kin) : nullptr;
     a.imag = imag;
-    a.inv_n = (T)(1.0 / (double)st.N);
+    a.inv_n = (T)(1.0 / (double)st.Nrep);      // transforms act on one replica
     a.k2h = st.d_k2h;
     a.partials = st.d_partials;
     a.ring = st.no_ring ? 0 : 1;
@@ -430,17 +430,25 @@ template <class T> ctap_status observe_raw(PlanState &st, const Cx<T> *psi, doub
     xa.flags = XY_RED_OBS | XY_OUT_MIXED;
     xa.partials = st.d_partials;
     CTAP_TRY(go_xy<T>(st, xa));
-    CTAP_TRY(go_other(st, "reduce", [&] { launch_reduce(st.d_partials, nxy, 5, st.d_red, st.stream); }));
+    // per-CTA partials are replica-major in both passes: one fixed-order sum per replica
+    const int B = st.batch, nxy_r = nxy / B, nz_r = nz_ / B;
+    CTAP_TRY(go_other(st, "reduce", [&] {
+        for (int b = 0; b < B; ++b)
+            launch_reduce(st.d_partials + (size_t)5 * nxy_r * b, nxy_r, 5, st.d_red + 8 * b,
+                          st.stream);
+    }));
     za.src = reinterpret_cast<const Cx<T> *>(st.d_work);
     za.dst = nullptr;
     za.observe = 1;
     za.partials = st.d_partials + (size_t)5 * nxy;
     CTAP_TRY(go_z<T>(st, za));
     CTAP_TRY(go_other(st, "reduce", [&] {
-        launch_reduce(st.d_partials + (size_t)5 * nxy, nz_, 1, st.d_red + 5, st.stream);
+        for (int b = 0; b < B; ++b)
+            launch_reduce(st.d_partials + (size_t)5 * nxy + (size_t)nz_r * b, nz_r, 1,
+                          st.d_red + 8 * b + 5, st.stream);
     }));
-    cudaError_t e = cudaMemcpyAsync(raw, st.d_red, 6 * sizeof(double), cudaMemcpyDeviceToHost,
-                                    st.stream);
+    cudaError_t e = cudaMemcpyAsync(raw, st.d_red, 8 * (size_t)B * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st.stream);
     if (e != cudaSuccess) return cuda_fail(st, e, "observables copy");
     return wait_stream(st, 0);
 }
@@ -449,7 +457,7 @@ ctap_status finish_observables(PlanState &st, const double *raw, double *out)
 {
     const double s2 = raw[0];
     out[0] = s2 * st.dV;
-    out[1] = s2 > 0 ? raw[5] / ((double)st.N * s2) : 0.0;
+    out[1] = s2 > 0 ? raw[5] / ((double)st.Nrep * s2) : 0.0;
     out[2] = s2 > 0 ? raw[1] / s2 : 0.0;
     for (int j = 0; j < 3; ++j) out[3 + j] = st.have_regions ? raw[2 + j] * st.dV : 0.0;
     for (int i = 0; i < 6; ++i)
@@ -682,8 +690,10 @@ ctap_status set_product(PlanState &st, const std::vector<double> &gy, const std:
     return CTAP_OK;
 }
 
+// mid: depth factor of the middle guide per replica (null: 1 for all)
 ctap_status set_guides_impl(PlanState &st, double V0, double s, const double *x1z,
-                            const double *x3z, double hw, int set_regions)
+                            const double *x3z, double hw, int set_regions,
+                            const double *mid = nullptr)
 {
     drop_graphs(st);
     if (!(s > 0) || !std::isfinite(V0) || !(hw > 0))
@@ -706,6 +716,21 @@ ctap_status set_guides_impl(PlanState &st, double V0, double s, const double *x1
             D1[(size_t)z * nx + x] = -V0 * std::exp(-d1 * d1 * inv2s2) * d1 / (s * s);
             D3[(size_t)z * nx + x] = -V0 * std::exp(-d3 * d3 * inv2s2) * d3 / (s * s);
         }
+    }
+    if (st.batch > 1 || mid) {
+        // replica b: -V0 (G1 + mid_b G2 + G3); G2 = exp(-x^2/2s^2) (centre 0)
+        std::vector<double> Hb((size_t)st.batch * nz * nx);
+        for (int b = 0; b < st.batch; ++b) {
+            const double m = mid ? mid[b] : 1.0;
+            for (int z = 0; z < nz; ++z)
+                for (int x = 0; x < nx; ++x) {
+                    const double xx = grid_point(x, nx, st.box[0], st.box[1]);
+                    const double g2 = std::exp(-xx * xx * inv2s2);
+                    Hb[((size_t)b * nz + z) * nx + x] =
+                        H[(size_t)z * nx + x] + V0 * (1.0 - m) * g2;
+                }
+        }
+        H.swap(Hb);
     }
     CTAP_TRY(set_product(st, gy, H));
     CTAP_TRY(upload64(st, &st.d_D1, D1));
@@ -763,7 +788,17 @@ const char *ctap_last_error(ctap_plan_t plan)
 ctap_status ctap_plan_create(int nx, int ny, int nz, const double *box, ctap_dtype dtype,
                              void *cuda_stream, ctap_plan_t *out)
 {
+    return ctap_plan_create_batched(nx, ny, nz, 1, box, dtype, cuda_stream, out);
+}
+
+ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const double *box,
+                                     ctap_dtype dtype, void *cuda_stream, ctap_plan_t *out)
+{
     if (!out) return CTAP_ERR_INVALID_ARG;
+    if (batch < 1 || batch > CTAP_MAX_BATCH) {
+        *out = nullptr;
+        return CTAP_ERR_INVALID_ARG;
+    }
     *out = nullptr;
     if (!box) return CTAP_ERR_INVALID_ARG;
     if (dtype != CTAP_C64 && dtype != CTAP_C128) return CTAP_ERR_DTYPE;
@@ -784,7 +819,9 @@ ctap_status ctap_plan_create(int nx, int ny, int nz, const double *box, ctap_dty
     st.dtype = dtype;
     st.stream = static_cast<cudaStream_t>(cuda_stream);
     st.esize = dtype == CTAP_C64 ? 8 : 16;
-    st.N = (long long)nx * ny * nz;
+    st.batch = batch;
+    st.Nrep = (long long)nx * ny * nz;
+    st.N = st.Nrep * batch;
     st.dV = (box[1] - box[0]) / nx * (box[3] - box[2]) / ny * (box[5] - box[4]) / nz;
     const int maxv = dtype == CTAP_C64 ? 32 : 16;
     const int emax = kNT * maxv;
@@ -814,9 +851,10 @@ ctap_status ctap_plan_create(int nx, int ny, int nz, const double *box, ctap_dty
     if ((s = dev_alloc(st, &q, np * sizeof(double))) != CTAP_OK) return bail(s);
     st.d_partials = static_cast<double *>(q);
     st.n_partials = np;
-    if ((s = dev_alloc(st, &q, 16 * sizeof(double))) != CTAP_OK) return bail(s);
+    // reductions: 8 doubles per replica, then the imaginary-time scale
+    if ((s = dev_alloc(st, &q, (8 * (size_t)batch + 8) * sizeof(double))) != CTAP_OK) return bail(s);
     st.d_red = static_cast<double *>(q);
-    st.d_scale = st.d_red + 8;
+    st.d_scale = st.d_red + 8 * (size_t)batch;
     *out = p;
     return CTAP_OK;
 }
@@ -850,6 +888,7 @@ ctap_status ctap_set_potential(ctap_plan_t plan, const double *V)
 {
     PlanState *st = S(plan);
     if (!st || !V) return CTAP_ERR_INVALID_ARG;
+    if (st->batch > 1) return fail(*st, CTAP_ERR_INVALID_ARG, "batched plans take the product form");
     clear_potential(*st);
     st->h_V.assign(V, V + st->N);
     for (double v : st->h_V)
@@ -868,6 +907,7 @@ ctap_status ctap_set_potential_separable(ctap_plan_t plan, const double *Vx, con
 {
     PlanState *st = S(plan);
     if (!st || !Vx || !Vy || !Vz) return CTAP_ERR_INVALID_ARG;
+    if (st->batch > 1) return fail(*st, CTAP_ERR_INVALID_ARG, "batched plans take the product form");
     clear_potential(*st);
     st->h_vsep.assign(Vx, Vx + st->nx);
     st->h_vsep.insert(st->h_vsep.end(), Vy, Vy + st->ny);
@@ -891,6 +931,12 @@ ctap_status ctap_set_potential_product(ctap_plan_t plan, const double *gy, const
         if (!std::isfinite(v)) return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite potential");
     for (double v : H)
         if (!std::isfinite(v)) return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite potential");
+    if (st->batch > 1) {                        // the same H for every replica
+        std::vector<double> Hb;
+        Hb.reserve(H.size() * st->batch);
+        for (int b = 0; b < st->batch; ++b) Hb.insert(Hb.end(), H.begin(), H.end());
+        H.swap(Hb);
+    }
     CTAP_TRY(set_product(*st, g, H));
     st->have_guides = false;
     st->have_spline = false;
@@ -907,12 +953,27 @@ ctap_status ctap_set_guides(ctap_plan_t plan, double V0, double s, const double 
     return CTAP_OK;
 }
 
+ctap_status ctap_set_guides_batched(ctap_plan_t plan, double V0, double s, const double *x1z,
+                                    const double *x3z, const double *mid_scale, double halfwidth,
+                                    int set_regions)
+{
+    PlanState *st = S(plan);
+    if (!st || !x1z || !x3z || !mid_scale) return CTAP_ERR_INVALID_ARG;
+    for (int b = 0; b < st->batch; ++b)
+        if (!std::isfinite(mid_scale[b]))
+            return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite middle-guide scale");
+    CTAP_TRY(set_guides_impl(*st, V0, s, x1z, x3z, halfwidth, set_regions, mid_scale));
+    st->have_spline = false;
+    return CTAP_OK;
+}
+
 ctap_status ctap_set_guides_spline(ctap_plan_t plan, double V0, double s, int nknots,
                                    const double *knots_z, const double *c12, const double *c23,
                                    double halfwidth, int set_regions)
 {
     PlanState *st = S(plan);
     if (!st || !knots_z || !c12 || !c23 || nknots < 2 || nknots > 64) return CTAP_ERR_INVALID_ARG;
+    if (st->batch > 1) return fail(*st, CTAP_ERR_INVALID_ARG, "spline controls need an unbatched plan");
     for (int i = 0; i + 1 < nknots; ++i)
         if (!(knots_z[i + 1] > knots_z[i]))
             return fail(*st, CTAP_ERR_INVALID_ARG, "knots must be strictly ascending");
@@ -976,7 +1037,7 @@ ctap_status ctap_density_xz(ctap_plan_t plan, const void *psi, double *out)
 {
     PlanState *st = S(plan);
     if (!st || !psi || !out) return CTAP_ERR_INVALID_ARG;
-    const size_t n = (size_t)st->nz * st->nx;
+    const size_t n = (size_t)st->batch * st->nz * st->nx;
     if (!st->d_dens) {
         void *q = nullptr;
         CTAP_TRY(dev_alloc(*st, &q, n * sizeof(double)));
@@ -1003,18 +1064,20 @@ ctap_status ctap_get_potential(ctap_plan_t plan, double *V)
     if (!st || !V) return CTAP_ERR_INVALID_ARG;
     if (st->vform == VF_NONE) return CTAP_ERR_NO_POTENTIAL;
     const int nx = st->nx, ny = st->ny, nz = st->nz;
-    for (int z = 0; z < nz; ++z)
+    for (int zb = 0; zb < nz * st->batch; ++zb) {
+        const int z = zb % nz;                  // replica-local z
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
-                const size_t i = ((size_t)z * ny + y) * nx + x;
+                const size_t i = ((size_t)zb * ny + y) * nx + x;
                 double v = 0.0;
                 if (st->vform == VF_DENSE) v = st->h_V[i];
                 else if (st->vform == VF_SEPARABLE)
                     v = st->h_vsep[x] + st->h_vsep[nx + y] + st->h_vsep[nx + ny + z];
-                else v = st->h_g[y] * st->h_H[(size_t)z * nx + x] +
+                else v = st->h_g[y] * st->h_H[(size_t)zb * nx + x] +
                          (st->h_vz.empty() ? 0.0 : st->h_vz[z]);
                 V[i] = v;
             }
+    }
     return CTAP_OK;
 }
 
@@ -1025,6 +1088,8 @@ ctap_status ctap_step(ctap_plan_t plan, void *psi, int nsteps, double dt, ctap_t
     if (mode != CTAP_REAL && mode != CTAP_IMAG && mode != CTAP_REAL_KVK) return CTAP_ERR_INVALID_ARG;
     if (st->vform == VF_NONE) return CTAP_ERR_NO_POTENTIAL;
     if (reinterpret_cast<uintptr_t>(psi) % st->esize) return fail(*st, CTAP_ERR_INVALID_ARG, "psi misaligned");
+    if (mode == CTAP_IMAG && st->batch > 1)
+        return fail(*st, CTAP_ERR_INVALID_ARG, "imaginary time needs an unbatched plan");
     if (st->dtype == CTAP_C64)
         return step_maybe_graph<float>(*st, static_cast<float2 *>(psi), nsteps, dt, (int)mode);
     return step_maybe_graph<double>(*st, static_cast<double2 *>(psi), nsteps, dt, (int)mode);
@@ -1034,12 +1099,14 @@ ctap_status ctap_observables(ctap_plan_t plan, const void *psi, double *out)
 {
     PlanState *st = S(plan);
     if (!st || !psi || !out) return CTAP_ERR_INVALID_ARG;
-    double raw[6];
+    std::vector<double> raw(8 * (size_t)st->batch);
     if (st->dtype == CTAP_C64)
-        CTAP_TRY(observe_raw<float>(*st, static_cast<const float2 *>(psi), raw));
+        CTAP_TRY(observe_raw<float>(*st, static_cast<const float2 *>(psi), raw.data()));
     else
-        CTAP_TRY(observe_raw<double>(*st, static_cast<const double2 *>(psi), raw));
-    return finish_observables(*st, raw, out);
+        CTAP_TRY(observe_raw<double>(*st, static_cast<const double2 *>(psi), raw.data()));
+    for (int b = 0; b < st->batch; ++b)
+        CTAP_TRY(finish_observables(*st, raw.data() + 8 * b, out + 6 * b));
+    return CTAP_OK;
 }
 
 ctap_status ctap_adjoint(ctap_plan_t plan, const void *psi0, int nsteps, double dt, int K,
@@ -1051,6 +1118,7 @@ ctap_status ctap_adjoint(ctap_plan_t plan, const void *psi0, int nsteps, double 
         return CTAP_ERR_INVALID_ARG;
     if (!st->have_spline || !st->have_regions)
         return fail(*st, CTAP_ERR_NO_POTENTIAL, "adjoint needs ctap_set_guides_spline");
+    if (st->batch > 1) return fail(*st, CTAP_ERR_INVALID_ARG, "adjoint needs an unbatched plan");
     if (st->dtype == CTAP_C64)
         return run_adjoint<float>(*st, static_cast<const float2 *>(psi0), nsteps, dt, K, guide, J,
                                   grad);

@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
     const Geom &g = a.g;
     const int t = threadIdx.x;
     const int z = blockIdx.x >> g.lgP, r = blockIdx.x & (g.P - 1);
+    const int zl = z & (g.nz - 1);          // replica-local z (z counts planes over the batch)
     const long long pbase = (long long)z * g.plane;
     const C2 *src = a.src + pbase;
     C2 *dst = a.dst + pbase;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
     const bool full = (flags & XY_KICK_FULL) != 0;
     const T tau = full ? k.tau_full : k.tau_half;
     // additive z-only term of the product form: one phase for the whole plane
-    const T thz = k.vz ? k.vz[z] * tau : T(0);
+    const T thz = k.vz ? k.vz[zl] * tau : T(0);
 
     auto swx = [](int x) { return RA * (x % RB) + x / RB; };     // natural x -> position
     auto unswx = [](int p) { return p / RA + RB * (p % RA); };   // position -> natural x
@@ -388,15 +389,15 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                     const double xq = g.box[0] + (double)x * g.dx;
                     bool in0 = false, in1 = false, in2 = false;
                     if (a.rd.xc) {
-                        in0 = fabs(xq - a.rd.xc[z]) < a.rd.hw;
-                        in1 = fabs(xq - a.rd.xc[g.nz + z]) < a.rd.hw;
-                        in2 = fabs(xq - a.rd.xc[2 * g.nz + z]) < a.rd.hw;
+                        in0 = fabs(xq - a.rd.xc[zl]) < a.rd.hw;
+                        in1 = fabs(xq - a.rd.xc[g.nz + zl]) < a.rd.hw;
+                        in2 = fabs(xq - a.rd.xc[2 * g.nz + zl]) < a.rd.hw;
                     }
                     const double hz =
                         (a.vform_obs == VF_PRODUCT) ? a.rd.H64[(long long)z * g.nx + x] : 0.0;
-                    const double vz64 = a.rd.vz64 ? a.rd.vz64[z] : 0.0;
+                    const double vz64 = a.rd.vz64 ? a.rd.vz64[zl] : 0.0;
                     const double vxz = (a.vform_obs == VF_SEPARABLE)
-                                           ? a.rd.Vsep[x] + a.rd.Vsep[g.nx + g.ny + z] : 0.0;
+                                           ? a.rd.Vsep[x] + a.rd.Vsep[g.nx + g.ny + zl] : 0.0;
 #pragma unroll
                     for (int rr = 0; rr < YA; ++rr) {
                         const int y = r + (i + YB * rr) * g.P;
@@ -422,8 +423,8 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                 } else if (kick) {
                     if (k.form == VF_SEPARABLE) {
                         const Lift<T> *tb = full ? k.sep_full : k.sep_half;
-                        const Lift<T> lx = tb[x], lz = tb[g.nx + g.ny + z];
-                        const Lift<T> hx = k.sep_half[x], hz = k.sep_half[g.nx + g.ny + z];
+                        const Lift<T> lx = tb[x], lz = tb[g.nx + g.ny + zl];
+                        const Lift<T> hx = k.sep_half[x], hz = k.sep_half[g.nx + g.ny + zl];
 #pragma unroll
                         for (int rr = 0; rr < YA; ++rr) {
                             const int jy = i + YB * rr;
@@ -587,7 +588,9 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
     C2 *sm = reinterpret_cast<C2 *>(smraw);
     const Geom &g = a.g;
     const int t = threadIdx.x;
-    const int kp = blockIdx.x >> g.nblk_lg, b = blockIdx.x & ((1 << g.nblk_lg) - 1);
+    const int tl = blockIdx.x & ((1 << g.lgzt) - 1);          // tile within the replica
+    const long long roff = (long long)(blockIdx.x >> g.lgzt) * g.rstride;
+    const int kp = tl >> g.nblk_lg, b = tl & ((1 << g.nblk_lg) - 1);
     // C >= 16: rows of 16 complex span all 32 banks; rotate W-column blocks by
     //          z so the W-lane groups of Z1/Z5 land on distinct banks.
     // C == 8:  two rows share the 32 banks; rotate column pairs by z/2 (Z1/Z5)
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
         }
     };
     const Lift<T> *wc = a.tw + g.cross_off;    // exp(-2 pi i e/ny)
-    const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
+    const long long colbase = roff + ((long long)(kp * P) << g.lgnx) + (b * W);
     // z twiddles exp(-2 pi i e/NZ) and z kinetic factors, staged in shared
     // memory (L1 would lose them to the streaming tile loads)
     constexpr int TILE = NZ * C + ((sizeof(T) == 4 && C == 8) ? (NZ / 32) * 8 : 0);   // + row-block padding
@@ -868,8 +871,10 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
     const int cdst = czl * C + ((cr * W + 2 * ch) ^ ((czl & SWM) * W));
     auto issue = [&](int i, int c0, int c1) {
         const int tile = blockIdx.x + i * G;
-        const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
-        const C2 *src = a.src + ((long long)(kp * P + cr) << g.lgnx) + b * W + 2 * ch +
+        const int tl = tile & ((1 << g.lgzt) - 1);
+        const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
+        const C2 *src = a.src + (long long)(tile >> g.lgzt) * g.rstride +
+                        ((long long)(kp * P + cr) << g.lgnx) + b * W + 2 * ch +
                         (long long)(c0 * CHZ + czl) * g.plane;
         const long long zstep = (long long)(NT / 8) * g.plane;
         for (int c = c0; c < c1; ++c) {
@@ -887,7 +892,8 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
     auto load_tabs = [&](int i) {
         if (t < W + 2 * P) {
             const int tile = blockIdx.x + i * G;
-            const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
+            const int tl = tile & ((1 << g.lgzt) - 1);
+            const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
             Lift<T> v;
             if (t < W) v = a.kin[b * W + t];
             else if (t < W + P) v = a.kin[g.nx + kp + ((t - W) << g.lgLy)];
@@ -909,7 +915,9 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
 
     for (int i = 0; i < nmine; ++i) {
         const int tile = blockIdx.x + i * G;
-        const int kp = tile >> g.nblk_lg, b = tile & nblk_mask;
+        const int tl = tile & ((1 << g.lgzt) - 1);
+        const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
+        const long long roff = (long long)(tile >> g.lgzt) * g.rstride;
         if (i + 1 < nmine) {
             issue(i + 1, 0, NCH / 2);
             load_tabs(i + 1);
@@ -926,7 +934,7 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
             int s = slot_of(i, zz / CHZ);
             return s * CHE + (zz % CHZ) * C + (col ^ ((zz & SWM) * W));
         };
-        const long long colbase = ((long long)(kp * P) << g.lgnx) + (b * W);
+        const long long colbase = roff + ((long long)(kp * P) << g.lgnx) + (b * W);
 
         // Z1: cross twiddle + forward P-point DFT, in place (two columns per task)
         for (int q = t; q < NZ * (W / 2); q += NT) {

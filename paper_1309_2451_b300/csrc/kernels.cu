@@ -37,11 +37,12 @@ template <int NQ> __device__ void block_sum_store(double (&acc)[NQ], double *out
 // psi <- exp(-i V tau) psi (real time) or exp(-V tau) psi (imaginary time)
 template <class T>
 __device__ __forceinline__ void kick_point(Cx<T> &v, const Kick<T> &k, const Geom &g, int x,
-                                           int y, int z, bool full)
+                                           int y, int z, int zl, bool full)
 {
+    // z: plane index over the batch (per-plane tables), zl: replica-local z
     if (k.form == VF_SEPARABLE) {
         const Lift<T> *t = full ? k.sep_full : k.sep_half;
-        const Lift<T> a = t[x], b = t[g.nx + y], c = t[g.nx + g.ny + z];
+        const Lift<T> a = t[x], b = t[g.nx + y], c = t[g.nx + g.ny + zl];
         if (k.imag) {
             const T f = a.f * b.f * c.f;
             v.x *= f;
@@ -57,7 +58,7 @@ __device__ __forceinline__ void kick_point(Cx<T> &v, const Kick<T> &k, const Geo
     } else {
         const T V = (k.form == VF_DENSE) ? k.Vd[((long long)z * g.ny + y) * g.nx + x]
                                          : k.g[y] * k.H[(long long)z * g.nx + x] +
-                                               (k.vz ? k.vz[z] : T(0));
+                                               (k.vz ? k.vz[zl] : T(0));
         const T th = V * (full ? k.tau_full : k.tau_half);
         if (k.imag) {
             const T f = dexp(-th);
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
     Cx<T> *sm = reinterpret_cast<Cx<T> *>(smraw);
     const Geom &g = a.g;
     const int z = blockIdx.x >> g.lgP, r = blockIdx.x & (g.P - 1);
+    const int zl = z & (g.nz - 1);
     const long long pbase = (long long)z * g.plane;
     const int E = g.Ly << g.lgnx;
     const int flags = a.flags;
@@ -100,16 +102,16 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
             double V = 0.0;
             if (a.vform_obs == VF_DENSE) V = (double)a.k.Vd[(pbase + ((long long)y << g.lgnx)) + x];
             else if (a.vform_obs == VF_PRODUCT)
-                V = a.rd.g64[y] * a.rd.H64[(long long)z * g.nx + x] + (a.rd.vz64 ? a.rd.vz64[z] : 0.0);
+                V = a.rd.g64[y] * a.rd.H64[(long long)z * g.nx + x] + (a.rd.vz64 ? a.rd.vz64[zl] : 0.0);
             else if (a.vform_obs == VF_SEPARABLE)
-                V = a.rd.Vsep[x] + a.rd.Vsep[g.nx + y] + a.rd.Vsep[g.nx + g.ny + z];
+                V = a.rd.Vsep[x] + a.rd.Vsep[g.nx + y] + a.rd.Vsep[g.nx + g.ny + zl];
             acc[0] += d;
             acc[1] += V * d;
             if (a.rd.xc) {
                 const double xq = g.box[0] + (double)x * g.dx;
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
-                    if (fabs(xq - a.rd.xc[q * g.nz + z]) < a.rd.hw) acc[2 + q] += d;
+                    if (fabs(xq - a.rd.xc[q * g.nz + zl]) < a.rd.hw) acc[2 + q] += d;
             }
         }
         block_sum_store<5>(acc, a.partials + (long long)blockIdx.x * 5);
@@ -141,12 +143,12 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
         for (int e = threadIdx.x; e < E; e += kNT) {
             const int j = e >> g.lgnx, x = e & (g.nx - 1), y = r + j * g.P;
             Cx<T> v = sm[j * g.pitchXY + x];
-            kick_point<T>(v, a.k, g, x, y, z, (flags & XY_KICK_FULL) != 0);
+            kick_point<T>(v, a.k, g, x, y, z, zl, (flags & XY_KICK_FULL) != 0);
             if (flags & XY_RED_NORM) nacc[0] += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
             if (flags & XY_STATE_OUT)
                 a.state_out[pbase + ((long long)y << g.lgnx) + x] = v;
             if (flags & XY_GRAD) grad_point(v, x, y);
-            if (flags & XY_KICK_SPLIT) kick_point<T>(v, a.k, g, x, y, z, false);
+            if (flags & XY_KICK_SPLIT) kick_point<T>(v, a.k, g, x, y, z, zl, false);
             sm[j * g.pitchXY + x] = v;
         }
         if (flags & XY_RED_NORM) block_sum_store<1>(nacc, a.partials + blockIdx.x);
@@ -179,14 +181,15 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
 // over the row classes r.  Result for ky = k' + Ly k2 goes to tile column
 // k2 w + xo.
 template <class T, int P>
-__device__ __forceinline__ void z_load_cross(const ZArgs<T> &a, Cx<T> *sm, int kp, int b)
+__device__ __forceinline__ void z_load_cross(const ZArgs<T> &a, Cx<T> *sm, int kp, int b,
+                                             long long roff)
 {
     const Geom &g = a.g;
     const Lift<T> *W = a.tw + g.cross_off;
     const int ntask = g.nz << g.lgw;
     for (int t = threadIdx.x; t < ntask; t += kNT) {
         const int zz = t >> g.lgw, xo = t & (g.w - 1);
-        const long long base = (long long)zz * g.plane + ((long long)(kp * P) << g.lgnx) +
+        const long long base = roff + (long long)zz * g.plane + ((long long)(kp * P) << g.lgnx) +
                                (b << g.lgw) + xo;
         Cx<T> v[P];
 #pragma unroll
@@ -203,14 +206,15 @@ __device__ __forceinline__ void z_load_cross(const ZArgs<T> &a, Cx<T> *sm, int k
 
 // Exact mirror of z_load_cross, storing the rows back.
 template <class T, int P>
-__device__ __forceinline__ void z_store_cross(const ZArgs<T> &a, const Cx<T> *sm, int kp, int b)
+__device__ __forceinline__ void z_store_cross(const ZArgs<T> &a, const Cx<T> *sm, int kp, int b,
+                                              long long roff)
 {
     const Geom &g = a.g;
     const Lift<T> *W = a.tw + g.cross_off;
     const int ntask = g.nz << g.lgw;
     for (int t = threadIdx.x; t < ntask; t += kNT) {
         const int zz = t >> g.lgw, xo = t & (g.w - 1);
-        const long long base = (long long)zz * g.plane + ((long long)(kp * P) << g.lgnx) +
+        const long long base = roff + (long long)zz * g.plane + ((long long)(kp * P) << g.lgnx) +
                                (b << g.lgw) + xo;
         Cx<T> v[P];
         sfor<P>([&](auto kc) {
@@ -231,14 +235,16 @@ __global__ void __launch_bounds__(kNT, 1) z_pass_kernel(const ZArgs<T> a)
     extern __shared__ __align__(16) unsigned char smraw[];
     Cx<T> *sm = reinterpret_cast<Cx<T> *>(smraw);
     const Geom &g = a.g;
-    const int kp = blockIdx.x >> g.nblk_lg, b = blockIdx.x & ((1 << g.nblk_lg) - 1);
+    const int tl = blockIdx.x & ((1 << g.lgzt) - 1);          // tile within the replica
+    const long long roff = (long long)(blockIdx.x >> g.lgzt) * g.rstride;
+    const int kp = tl >> g.nblk_lg, b = tl & ((1 << g.nblk_lg) - 1);
 
     switch (g.P) {
-    case 1: z_load_cross<T, 1>(a, sm, kp, b); break;
-    case 2: z_load_cross<T, 2>(a, sm, kp, b); break;
-    case 4: z_load_cross<T, 4>(a, sm, kp, b); break;
-    case 8: z_load_cross<T, 8>(a, sm, kp, b); break;
-    default: z_load_cross<T, 16>(a, sm, kp, b); break;
+    case 1: z_load_cross<T, 1>(a, sm, kp, b, roff); break;
+    case 2: z_load_cross<T, 2>(a, sm, kp, b, roff); break;
+    case 4: z_load_cross<T, 4>(a, sm, kp, b, roff); break;
+    case 8: z_load_cross<T, 8>(a, sm, kp, b, roff); break;
+    default: z_load_cross<T, 16>(a, sm, kp, b, roff); break;
     }
     __syncthreads();
 
@@ -286,11 +292,11 @@ __global__ void __launch_bounds__(kNT, 1) z_pass_kernel(const ZArgs<T> a)
     axis_inv<MAXV, kNT, T>(sm, lz, g.lgC, g.apz, a.tw);
 
     switch (g.P) {
-    case 1: z_store_cross<T, 1>(a, sm, kp, b); break;
-    case 2: z_store_cross<T, 2>(a, sm, kp, b); break;
-    case 4: z_store_cross<T, 4>(a, sm, kp, b); break;
-    case 8: z_store_cross<T, 8>(a, sm, kp, b); break;
-    default: z_store_cross<T, 16>(a, sm, kp, b); break;
+    case 1: z_store_cross<T, 1>(a, sm, kp, b, roff); break;
+    case 2: z_store_cross<T, 2>(a, sm, kp, b, roff); break;
+    case 4: z_store_cross<T, 4>(a, sm, kp, b, roff); break;
+    case 8: z_store_cross<T, 8>(a, sm, kp, b, roff); break;
+    default: z_store_cross<T, 16>(a, sm, kp, b, roff); break;
     }
 }
 
@@ -356,7 +362,7 @@ template <class T>
 __global__ void density_xz_kernel(const Cx<T> *psi, const Geom g, double dy, double *out)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)g.nz * g.nx) return;
+    if (i >= (long long)g.batch * g.nz * g.nx) return;
     const int z = (int)(i >> g.lgnx), x = (int)(i & (g.nx - 1));
     const Cx<T> *p = psi + (long long)z * g.plane + x;
     double acc = 0.0;
@@ -368,8 +374,8 @@ __global__ void density_xz_kernel(const Cx<T> *psi, const Geom g, double dy, dou
 }
 
 // -------------------------------------------------------------- launchers
-int xy_grid(const Geom &g) { return g.nz * g.P; }
-int z_grid(const Geom &g) { return g.Ly << g.nblk_lg; }
+int xy_grid(const Geom &g) { return g.batch * g.nz * g.P; }
+int z_grid(const Geom &g) { return g.batch << g.lgzt; }
 size_t xy_smem(const Geom &g, int esize) { return (size_t)g.Ly * g.pitchXY * esize; }
 size_t z_smem(const Geom &g, int esize) { return (size_t)g.nz * g.pitchZ * esize; }
 int mask_blocks(const Geom &g)
@@ -433,7 +439,7 @@ void launch_mask(const Cx<T> *psi, Cx<T> *lam, const Geom &g, const double *xcj,
 template <class T>
 void launch_density_xz(const Cx<T> *psi, const Geom &g, double dy, double *out, cudaStream_t st)
 {
-    const long long n = (long long)g.nz * g.nx;
+    const long long n = (long long)g.batch * g.nz * g.nx;
     density_xz_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, g, dy, out);
 }
 

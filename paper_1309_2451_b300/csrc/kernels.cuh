@@ -64,6 +64,12 @@ struct Geom {
     int fast_x_off;         // offset of exp(-2 pi i e/nx), e < nx (fast passes)
     int fast_z_off;         // offset of exp(-2 pi i e/nz), e < nz (fast passes)
     int fast_y_off;         // offset of exp(-2 pi i e/Ly), e < Ly (fast passes)
+    // batched replicas: psi is [batch][nz][ny][nx]; the XY pass sees batch*nz
+    // planes (plane index zall, replica-local z = zall mod nz), the Z pass
+    // batch * 2^lgzt tiles (replica = tile >> lgzt)
+    int batch;
+    int lgzt;               // log2(Z tiles per replica) = lgLy + nblk_lg
+    long long rstride;      // elements per replica = nz * plane
 };
 
 template <class T> struct Kick {

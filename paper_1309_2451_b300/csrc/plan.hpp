@@ -43,7 +43,9 @@ struct PlanState {
     ctap_dtype dtype;
     cudaStream_t stream;
     int esize;
-    long long N;
+    long long N;                   // points of all replicas (batch * Nrep)
+    long long Nrep;                // points of one replica
+    int batch = 1;                 // independent replicas in one psi
     double dV;
     Geom geom;
     int timeout_ms = 60000;

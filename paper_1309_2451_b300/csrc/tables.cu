@@ -129,6 +129,9 @@ void build_geometry(PlanState &p, int emax, int maxv)
     g.pitchZ = g.C;
     g.nblk_lg = lg2(p.nx / w);
     g.plane = (long long)p.nx * p.ny;
+    g.batch = p.batch;
+    g.lgzt = g.lgLy + g.nblk_lg;
+    g.rstride = g.plane * p.nz;
     for (int i = 0; i < 6; ++i) g.box[i] = p.box[i];
     g.dx = (p.box[1] - p.box[0]) / p.nx;
     const size_t es = p.esize;

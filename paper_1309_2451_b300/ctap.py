@@ -41,6 +41,8 @@ def lib():
     i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
     sig = {
         "ctap_plan_create": [i, i, i, _dp, i, _vp, ctypes.POINTER(_vp)],
+        "ctap_plan_create_batched": [i, i, i, i, _dp, i, _vp, ctypes.POINTER(_vp)],
+        "ctap_set_guides_batched": [_vp, d, d, _dp, _dp, _dp, d, i],
         "ctap_plan_destroy": [_vp],
         "ctap_set_potential": [_vp, _dp],
         "ctap_set_potential_separable": [_vp, _dp, _dp, _dp],
@@ -82,7 +84,7 @@ def exported_symbols():
             "ctap_adjoint", "ctap_sync", "ctap_set_timeout", "ctap_launch_count",
             "ctap_set_profiling", "ctap_pass_times", "ctap_plan_info", "ctap_status_string",
             "ctap_last_error", "ctap_version", "ctap_norm_noalloc", "ctap_add_potential_z",
-            "ctap_density_xz"]
+            "ctap_density_xz", "ctap_plan_create_batched", "ctap_set_guides_batched"]
 
 
 def _f64(a, n=None):
@@ -99,13 +101,17 @@ def _p(a):
 class Plan:
     """A split-step plan for psi of shape (nz, ny, nx) on `box`.
 
-    dtype "c64" (FP32 bulk, FP64 tables and reductions) or "c128"."""
+    dtype "c64" (FP32 bulk, FP64 tables and reductions) or "c128".  batch > 1
+    makes a plan for `batch` independent replicas, psi of shape
+    (batch, nz, ny, nx) (product-form potentials, real time)."""
 
-    def __init__(self, shape, box, dtype="c64", stream=None):
+    def __init__(self, shape, box, dtype="c64", stream=None, batch=1):
         import torch
         self._torch = torch
         nz, ny, nx = (int(s) for s in shape)
         self.shape = (nz, ny, nx)
+        self.batch = int(batch)
+        self.psi_shape = self.shape if self.batch == 1 else (self.batch,) + self.shape
         self.box = tuple(float(b) for b in box)
         self.dtype = {"c64": CTAP_C64, "c128": CTAP_C128,
                       torch.complex64: CTAP_C64, torch.complex128: CTAP_C128}[dtype]
@@ -115,8 +121,9 @@ class Plan:
         self.stream = stream
         h = _vp()
         self._h = None
-        self._check(lib().ctap_plan_create(nx, ny, nz, _p(_f64(self.box, 6)), self.dtype,
-                                           _vp(stream.cuda_stream), ctypes.byref(h)))
+        self._check(lib().ctap_plan_create_batched(nx, ny, nz, self.batch, _p(_f64(self.box, 6)),
+                                                   self.dtype, _vp(stream.cuda_stream),
+                                                   ctypes.byref(h)))
         self._h = h
 
     # ---------------------------------------------------------------- util
@@ -144,13 +151,13 @@ class Plan:
             raise TypeError("psi must be a CUDA tensor")
         if psi.dtype != self.torch_dtype:
             raise CtapError(3, f"psi is {psi.dtype}, plan is {self.torch_dtype}")
-        if tuple(psi.shape) != self.shape or not psi.is_contiguous():
-            raise ValueError(f"psi must be a contiguous {self.shape} tensor")
+        if tuple(psi.shape) != self.psi_shape or not psi.is_contiguous():
+            raise ValueError(f"psi must be a contiguous {self.psi_shape} tensor")
         return _vp(psi.data_ptr())
 
     # ----------------------------------------------------------- potential
     def set_potential(self, V):
-        self._check(lib().ctap_set_potential(self._h, _p(_f64(V, int(np.prod(self.shape))))))
+        self._check(lib().ctap_set_potential(self._h, _p(_f64(V, int(np.prod(self.psi_shape))))))
 
     def set_potential_separable(self, Vx, Vy, Vz):
         nz, ny, nx = self.shape
@@ -168,6 +175,13 @@ class Plan:
                                           _p(_f64(x3z, nz)), float(halfwidth),
                                           1 if set_regions else 0))
 
+    def set_guides_batched(self, V0, s, x1z, x3z, mid_scale, halfwidth=1.5, set_regions=True):
+        """Guides with the middle guide's depth scaled by mid_scale[b] in replica b."""
+        nz = self.shape[0]
+        self._check(lib().ctap_set_guides_batched(self._h, float(V0), float(s), _p(_f64(x1z, nz)),
+                                                  _p(_f64(x3z, nz)), _p(_f64(mid_scale, self.batch)),
+                                                  float(halfwidth), 1 if set_regions else 0))
+
     def set_guides_spline(self, V0, s, knots, c12, c23, halfwidth=1.5, set_regions=True):
         k = _f64(knots)
         self._check(lib().ctap_set_guides_spline(self._h, float(V0), float(s), k.size, _p(k),
@@ -180,7 +194,7 @@ class Plan:
         self._check(lib().ctap_add_potential_z(self._h, _p(_f64(Vz, self.shape[0]))))
 
     def get_potential(self):
-        V = np.empty(self.shape)
+        V = np.empty(self.psi_shape)
         self._check(lib().ctap_get_potential(self._h, _p(V)))
         return V
 
@@ -200,14 +214,15 @@ class Plan:
 
     def density_xz(self, psi):
         """sum_y |psi|^2 dy as an (nz, nx) FP64 array (Fig. 5)."""
-        out = np.zeros((self.shape[0], self.shape[2]))
+        out = np.zeros((self.batch * self.shape[0], self.shape[2]))
         self._check(lib().ctap_density_xz(self._h, self._psi(psi), _p(out)))
-        return out
+        return out if self.batch == 1 else out.reshape(self.batch, self.shape[0], self.shape[2])
 
     def observables(self, psi):
-        out = np.zeros(6)
+        """[norm, <T>, <V>, P_1, P_2, P_3]; shape (batch, 6) for batched plans."""
+        out = np.zeros(6 * self.batch)
         self._check(lib().ctap_observables(self._h, self._psi(psi), _p(out)))
-        return out
+        return out if self.batch == 1 else out.reshape(self.batch, 6)
 
     def adjoint(self, psi0, nsteps, dt, K=32, guide=3):
         m = getattr(self, "nknots", 0)

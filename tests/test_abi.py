@@ -72,6 +72,9 @@ def test_plan_create_rejects_bad_args_without_gpu(libctap):
     good = (ctypes.c_double * 6)(-1, 1, -1, 1, -1, 1)
     assert libctap.ctap_plan_create(8, 8, 8, good, 7, None, ctypes.byref(h)) == 3
     assert libctap.ctap_plan_create(8, 8, 8, None, 0, None, ctypes.byref(h)) == 1
+    for batch in (0, -3, 1025):
+        assert libctap.ctap_plan_create_batched(8, 8, 8, batch, good, 0, None, ctypes.byref(h)) == 1
+        assert not h.value
     assert libctap.ctap_plan_destroy(None) == 1
     assert libctap.ctap_step(None, None, 1, 0.1, 0) == 1
     assert libctap.ctap_sync(None, 10) == 1

@@ -168,3 +168,81 @@ def test_density_xz_matches_oracle(ctap, shape, dtype):
     assert np.allclose(got, want, rtol=1e-12, atol=1e-300)
     # deterministic
     assert np.array_equal(got, plan.density_xz(psi))
+
+
+# --------------------------------------------------- batched replicas (N3)
+BATCH_SHAPES = [(256, 64, 64), (64, 32, 16), (1024, 256, 64)]
+
+
+@pytest.mark.parametrize("shape", BATCH_SHAPES)
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batched_replicas_match_separate_plans_and_oracle(ctap, shape, dtype):
+    """Three replicas with different middle-guide depths (the Fig. 6 sweep
+    variable) advanced by one batched plan: each equals its own unbatched
+    plan bitwise (same kernels per replica) and the oracle with that
+    replica's potential; observables per replica match."""
+    if dtype == "c128" and shape[0] == 1024:
+        pytest.skip("complex128 covered on the smaller shapes")
+    box = wl.CTAP_BOX
+    z = wl.axis(shape[0], box[4], box[5])
+    c = wl.guide_centres(z)
+    mids = [0.8, 1.0, 1.25]
+    B = len(mids)
+    psis = np.stack([guide_state(shape, box, 30 + b) for b in range(B)])
+    plan = ctap.Plan(shape, box, dtype, batch=B)
+    plan.set_guides_batched(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], mids, wl.POP_HALFWIDTH)
+    plan.add_potential_z(wl.trap_z(z))
+    psi = to_dev(psis, dtype)
+    plan.step(psi, 4, 0.0025)
+    got = psi.cpu().numpy()
+    obs = plan.observables(psi)
+    assert obs.shape == (B, 6)
+    Vall = plan.get_potential()
+    nsteps_oracle = 4 if shape[0] < 1024 else 1
+    for b, m in enumerate(mids):
+        single = ctap.Plan(shape, box, dtype)
+        single.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+        G2 = np.exp(-wl.axis(shape[2], box[0], box[1]) ** 2 / (2 * wl.SIGMA_GUIDE ** 2))
+        gy = np.exp(-wl.axis(shape[1], box[2], box[3]) ** 2 / (2 * wl.SIGMA_GUIDE ** 2))
+        V = oracle.ctap_potential(shape, box, wl.V0, wl.SIGMA_GUIDE, c[0], c[2]) \
+            + wl.V0 * (1.0 - m) * gy[None, :, None] * G2[None, None, :] \
+            + wl.trap_z(z)[:, None, None]
+        assert np.allclose(Vall[b], V, rtol=1e-13, atol=1e-12)
+        if m == 1.0:
+            single.add_potential_z(wl.trap_z(z))
+            s1 = to_dev(psis[b], dtype)
+            single.step(s1, 4, 0.0025)
+            assert np.array_equal(s1.cpu().numpy(), got[b])
+        if nsteps_oracle == 4:
+            ref = oracle.step(psis[b], V, box, 0.0025, 4)
+            assert rel(got[b].astype(complex), ref) < (1e-6 if dtype == "c64" else 1e-13)
+            want = oracle.observables(ref, V, box, c, wl.POP_HALFWIDTH)
+            assert np.allclose(obs[b], want, rtol=1e-5 if dtype == "c64" else 1e-11, atol=1e-9)
+    dens = plan.density_xz(psi)
+    assert dens.shape == (B, shape[0], shape[2])
+    for b in range(B):
+        assert np.allclose(dens[b], oracle.density_xz(got[b].astype(complex), box), rtol=1e-12,
+                           atol=1e-300)
+
+
+def test_batched_plan_restrictions(ctap):
+    shape, box = (16, 16, 16), wl.CTAP_BOX
+    plan = ctap.Plan(shape, box, "c64", batch=2)
+    with pytest.raises(ctap.CtapError) as e:
+        plan.set_potential(np.zeros((2,) + shape))
+    assert e.value.code == 1
+    with pytest.raises(ctap.CtapError) as e:
+        plan.set_potential_separable(np.zeros(16), np.zeros(16), np.zeros(16))
+    assert e.value.code == 1
+    z = wl.axis(16, box[4], box[5])
+    c = wl.guide_centres(z)
+    plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2])
+    psi = to_dev(np.zeros((2,) + shape, complex), "c64")
+    with pytest.raises(ctap.CtapError) as e:
+        plan.step(psi, 1, 0.01, imag=True)
+    assert e.value.code == 1
+    with pytest.raises(ctap.CtapError) as e:
+        plan.set_guides_spline(wl.V0, wl.SIGMA_GUIDE, wl.KNOTS_Z, *wl.spline_controls())
+    assert e.value.code == 1
+    with pytest.raises(ValueError):
+        plan.step(to_dev(np.zeros(shape, complex), "c64"), 1, 0.01)
