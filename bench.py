@@ -263,7 +263,7 @@ def time_variants(torch, wl, device, stream, plan, psi, reps=4):
     return out
 
 
-def time_batched(torch, wl, device, stream, B=10, shape=(256, 64, 128), steps=200):
+def time_batched(torch, wl, device, stream, B=16, shape=(128, 64, 64), steps=200):
     """The parameter sweep of Fig. 6 as batched replicas: B middle-guide
     depths on a small grid advanced by one batched plan, against the same B
     runs one plan at a time (replica-steps per second)."""
