@@ -524,6 +524,15 @@ def run_ours(a):
             "fp32_speedup": (1000.0 / (ms / (a.steps * SPLIT))) / (1000.0 / ms64),
             "dtype": "f64", "obs": [float(x) for x in r64["obs"]]}
         del r64
+        rdf = time_path(ctap, wl, torch, "c128df", SPLIT_FP64, max(2, a.steps // 10), 1, device,
+                        stream)
+        msdf = rdf["ms"] / (max(2, a.steps // 10) * SPLIT_FP64)
+        extra["fp64_df_path"] = {
+            "steps_per_s": 1000.0 / msdf, "ms_per_step": msdf,
+            "arithmetic": "double-float (FP32 pairs, ~48-bit significands) on complex128 psi",
+            "speedup_over_fp64": ms64 / msdf,
+            "obs": [float(x) for x in rdf["obs"]]}
+        del rdf
     if rank == 0 and not a.no_extras:
         extra["rows"] = time_rows(ctap, wl, torch, device, stream)
         extra["variants"] = time_variants(torch, wl, device, stream, res["plan"], res["psi"])

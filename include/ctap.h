@@ -45,7 +45,14 @@ extern "C" {
 
 typedef struct ctap_plan *ctap_plan_t;          /* opaque, library-owned */
 
-typedef enum { CTAP_C64 = 0, CTAP_C128 = 1 } ctap_dtype;
+/* Precision of a plan.  CTAP_C64: complex64 psi, FP32 transforms.
+ * CTAP_C128: complex128 psi, FP64 transforms.  CTAP_C128_DF: complex128 psi,
+ * transforms in double-float arithmetic (pairs of FP32 numbers, about 48
+ * significant bits; B300's FP32 rate is many times its FP64 rate): psi is
+ * converted to the double-float form on entry to ctap_step and back on exit
+ * (both forms take 16 bytes per value).  ctap_adjoint needs CTAP_C64 or
+ * CTAP_C128. */
+typedef enum { CTAP_C64 = 0, CTAP_C128 = 1, CTAP_C128_DF = 2 } ctap_dtype;
 /* Time stepping of ctap_step: real time in the symmetric order V/2 K V/2
  * (the default), imaginary time in the same order, or real time in the
  * order K/2 V K/2 (the alternative Strang ordering). */

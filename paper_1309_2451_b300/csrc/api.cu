@@ -639,7 +639,9 @@ template <class T> ctap_status upload_as(PlanState &st, void **d, const std::vec
 
 ctap_status upload_prec(PlanState &st, void **d, const std::vector<double> &h)
 {
-    return st.dtype == CTAP_C64 ? upload_as<float>(st, d, h) : upload_as<double>(st, d, h);
+    if (st.dtype == CTAP_C64) return upload_as<float>(st, d, h);
+    if (st.dtype == CTAP_C128_DF) return upload_as<df>(st, d, h);
+    return upload_as<double>(st, d, h);
 }
 
 ctap_status upload64(PlanState &st, double **d, const std::vector<double> &h)
@@ -801,7 +803,7 @@ ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const do
     }
     *out = nullptr;
     if (!box) return CTAP_ERR_INVALID_ARG;
-    if (dtype != CTAP_C64 && dtype != CTAP_C128) return CTAP_ERR_DTYPE;
+    if (dtype != CTAP_C64 && dtype != CTAP_C128 && dtype != CTAP_C128_DF) return CTAP_ERR_DTYPE;
     for (int i = 0; i < 3; ++i)
         if (!(box[2 * i + 1] > box[2 * i]) || !std::isfinite(box[2 * i]) ||
             !std::isfinite(box[2 * i + 1]))
@@ -826,7 +828,7 @@ ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const do
     const int maxv = dtype == CTAP_C64 ? 32 : 16;
     const int emax = kNT * maxv;
     const char *fg = std::getenv("CTAP_FORCE_GENERIC");
-    st.force_generic = fg && fg[0] == '1';
+    st.force_generic = (fg && fg[0] == '1') || dtype == CTAP_C128_DF;   // double-float: generic passes
     const char *nr = std::getenv("CTAP_NO_RING");
     st.no_ring = nr && nr[0] == '1';
     try {
@@ -1047,7 +1049,7 @@ ctap_status ctap_density_xz(ctap_plan_t plan, const void *psi, double *out)
     CTAP_TRY(go_other(*st, "density", [&] {
         if (st->dtype == CTAP_C64)
             launch_density_xz<float>(static_cast<const float2 *>(psi), st->geom, dy, st->d_dens,
-                                     st->stream);
+                                     st->stream);                    // (complex128 for both others)
         else
             launch_density_xz<double>(static_cast<const double2 *>(psi), st->geom, dy, st->d_dens,
                                       st->stream);
@@ -1092,6 +1094,13 @@ ctap_status ctap_step(ctap_plan_t plan, void *psi, int nsteps, double dt, ctap_t
         return fail(*st, CTAP_ERR_INVALID_ARG, "imaginary time needs an unbatched plan");
     if (st->dtype == CTAP_C64)
         return step_maybe_graph<float>(*st, static_cast<float2 *>(psi), nsteps, dt, (int)mode);
+    if (st->dtype == CTAP_C128_DF) {
+        // complex128 in and out; double-float in between (same 16 bytes per value)
+        if (nsteps == 0) return CTAP_OK;
+        CTAP_TRY(go_other(*st, "to double-float", [&] { launch_c128_to_df(psi, st->N, st->stream); }));
+        CTAP_TRY(step_maybe_graph<df>(*st, static_cast<df2 *>(psi), nsteps, dt, (int)mode));
+        return go_other(*st, "from double-float", [&] { launch_df_to_c128(psi, st->N, st->stream); });
+    }
     return step_maybe_graph<double>(*st, static_cast<double2 *>(psi), nsteps, dt, (int)mode);
 }
 
@@ -1100,10 +1109,18 @@ ctap_status ctap_observables(ctap_plan_t plan, const void *psi, double *out)
     PlanState *st = S(plan);
     if (!st || !psi || !out) return CTAP_ERR_INVALID_ARG;
     std::vector<double> raw(8 * (size_t)st->batch);
-    if (st->dtype == CTAP_C64)
+    if (st->dtype == CTAP_C64) {
         CTAP_TRY(observe_raw<float>(*st, static_cast<const float2 *>(psi), raw.data()));
-    else
+    } else if (st->dtype == CTAP_C128_DF) {
+        // a double-float copy of the complex128 psi in the work buffer, observed in place
+        CTAP_TRY(ensure_work(*st));
+        CTAP_TRY(go_other(*st, "to double-float", [&] {
+            launch_c128_to_df_copy(psi, st->d_work, st->N, st->stream);
+        }));
+        CTAP_TRY(observe_raw<df>(*st, static_cast<const df2 *>(st->d_work), raw.data()));
+    } else {
         CTAP_TRY(observe_raw<double>(*st, static_cast<const double2 *>(psi), raw.data()));
+    }
     for (int b = 0; b < st->batch; ++b)
         CTAP_TRY(finish_observables(*st, raw.data() + 8 * b, out + 6 * b));
     return CTAP_OK;
@@ -1119,6 +1136,8 @@ ctap_status ctap_adjoint(ctap_plan_t plan, const void *psi0, int nsteps, double 
     if (!st->have_spline || !st->have_regions)
         return fail(*st, CTAP_ERR_NO_POTENTIAL, "adjoint needs ctap_set_guides_spline");
     if (st->batch > 1) return fail(*st, CTAP_ERR_INVALID_ARG, "adjoint needs an unbatched plan");
+    if (st->dtype == CTAP_C128_DF)
+        return fail(*st, CTAP_ERR_DTYPE, "adjoint runs in complex64 or complex128");
     if (st->dtype == CTAP_C64)
         return run_adjoint<float>(*st, static_cast<const float2 *>(psi0), nsteps, dt, K, guide, J,
                                   grad);

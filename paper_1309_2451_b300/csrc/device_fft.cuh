@@ -24,11 +24,14 @@
 #include <type_traits>
 #include <utility>
 
+#include "dfloat.cuh"
+
 namespace ctap {
 
 template <class T> struct CxT;
 template <> struct CxT<float> { using type = float2; };
 template <> struct CxT<double> { using type = double2; };
+template <> struct CxT<df> { using type = df2; };     // double-float complex (16 bytes)
 template <class T> using Cx = typename CxT<T>::type;
 
 // Rotation by phi with |phi| <= pi/2 times a sign s = +-1, in lifting form:
@@ -73,6 +76,8 @@ template <int N, class F> __device__ __forceinline__ void sfor(F &&f)
     sfor_impl(f, std::make_integer_sequence<int, N>{});
 }
 
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return ::exp(x); }
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
@@ -101,6 +106,19 @@ template <class T> __device__ __forceinline__ void lift_b(Cx<T> &v, const Lift<T
     v.x *= w.s;
     v.y *= w.s;
     rot_b<T>(v, w.p, w.u);
+}
+// double-float: the half-turn sign s = +-1 is applied exactly
+template <> __device__ __forceinline__ void lift_f<df>(df2 &v, const Lift<df> &w)
+{
+    rot_f<df>(v, w.p, w.u);
+    v.x = sign_mul(v.x, w.s);
+    v.y = sign_mul(v.y, w.s);
+}
+template <> __device__ __forceinline__ void lift_b<df>(df2 &v, const Lift<df> &w)
+{
+    v.x = sign_mul(v.x, w.s);
+    v.y = sign_mul(v.y, w.s);
+    rot_b<df>(v, w.p, w.u);
 }
 
 // Twiddle exp(-2 pi i J/R) of a radix-2 level of size R, J < R/2, reduced to
@@ -353,6 +371,37 @@ __device__ __forceinline__ void lift_from_angle(double a, double &p, double &u, 
     sn *= h;
     p = -sn / cs;
     u = 2.0 * sn * cs;
+}
+
+// double-float kick coefficients for |th| <= 0.1: p = -tan(-th/2), u = sin(-th)
+// from their odd Taylor series in double-float arithmetic (terms through
+// th^11, below 2^-48 relative)
+__device__ __forceinline__ void lift_small(df th, df &p, df &u)
+{
+    const df a = -th, a2 = a * a;
+    df s = fmadd(a2, df(-2.5052108385441720e-08), df(2.7557319223985893e-06));
+    s = fmadd(a2, s, df(-1.9841269841269841e-04));
+    s = fmadd(a2, s, df(8.3333333333333333e-03));
+    s = fmadd(a2, s, df(-1.6666666666666667e-01));
+    u = fmadd(a2 * a, s, a);
+    const df h = mul_f(a, 0.5f), h2 = h * h;
+    df t = fmadd(h2, df(3.5921280365724810e-03), df(8.8632355299021966e-03));
+    t = fmadd(h2, t, df(2.1869488536155203e-02));
+    t = fmadd(h2, t, df(5.3968253968253968e-02));
+    t = fmadd(h2, t, df(1.3333333333333333e-01));
+    t = fmadd(h2, t, df(3.3333333333333333e-01));
+    p = -fmadd(h2 * h, t, h);
+}
+
+// double-float angle: reduced and evaluated in FP64 (kicks use the
+// double-float series above for small angles instead)
+__device__ __forceinline__ void lift_from_angle(df a, df &p, df &u, df &s)
+{
+    double pd, ud, sd;
+    lift_from_angle(static_cast<double>(a), pd, ud, sd);
+    p = df(pd);
+    u = df(ud);
+    s = df(sd);
 }
 
 }  // namespace ctap

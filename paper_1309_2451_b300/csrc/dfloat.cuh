@@ -1,0 +1,113 @@
+// dfloat.cuh -- double-float ("double-word") arithmetic: a value is the
+// unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2, about
+// 48 significant bits.  B300 runs FP32 at many times its FP64 rate, so the
+// transforms of the complex128-accuracy path can run in this arithmetic.
+//
+// Building blocks (error-free transformations and the double-word
+// algorithms with proven bounds of Joldes, Muller and Popescu, "Tight and
+// rigorous error bounds for basic building blocks of double-word
+// arithmetic", ACM TOMS 44(2), 2017):
+//   two_sum        a + b = s + e exactly (6 operations, any a, b)
+//   fast_two_sum   the same when |a| >= |b| (3 operations)
+//   two_prod       a b = p + e exactly with one FMA
+//   add            DWPlusDW, relative error <= 3 u^2        (u = 2^-24)
+//   mul            DWTimesDW with FMA, relative error <= 5 u^2
+//   mul by FP32    DWTimesFP with FMA, relative error <= 2 u^2
+// No FP32 rounding may be reassociated or fused here: the FMAs are explicit
+// and the sums contain no products the compiler could contract.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ctap {
+
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr df(double d)
+        : hi(static_cast<float>(d)), lo(static_cast<float>(d - static_cast<double>(static_cast<float>(d)))) {}
+    __host__ __device__ constexpr df(float f) : hi(f), lo(0.0f) {}
+    __host__ __device__ constexpr df(int i) : hi(static_cast<float>(i)), lo(0.0f) {}
+    __host__ __device__ explicit operator double() const
+    {
+        return static_cast<double>(hi) + static_cast<double>(lo);
+    }
+};
+
+struct alignas(16) df2 {
+    df x, y;
+};
+
+namespace dfw {
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+}  // namespace dfw
+
+__device__ __forceinline__ df operator+(df x, df y)
+{
+    float sh, sl, th, tl, vh, vl, zh, zl;
+    dfw::two_sum(x.hi, y.hi, sh, sl);
+    dfw::two_sum(x.lo, y.lo, th, tl);
+    const float c = __fadd_rn(sl, th);
+    dfw::fast_two_sum(sh, c, vh, vl);
+    const float w = __fadd_rn(tl, vl);
+    dfw::fast_two_sum(vh, w, zh, zl);
+    return df(zh, zl);
+}
+__device__ __forceinline__ df operator-(df x) { return df(-x.hi, -x.lo); }
+__device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
+__device__ __forceinline__ df operator*(df x, df y)
+{
+    float ch, cl1;
+    dfw::two_prod(x.hi, y.hi, ch, cl1);
+    const float tl0 = __fmul_rn(x.lo, y.lo);
+    const float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+    const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+    const float cl3 = __fadd_rn(cl1, cl2);
+    float zh, zl;
+    dfw::fast_two_sum(ch, cl3, zh, zl);
+    return df(zh, zl);
+}
+// product with an FP32 number (DWTimesFP)
+__device__ __forceinline__ df mul_f(df x, float y)
+{
+    float ch, cl1;
+    dfw::two_prod(x.hi, y, ch, cl1);
+    const float cl3 = __fmaf_rn(x.lo, y, cl1);
+    float zh, zl;
+    dfw::fast_two_sum(ch, cl3, zh, zl);
+    return df(zh, zl);
+}
+__device__ __forceinline__ df &operator+=(df &x, df y) { return x = x + y; }
+__device__ __forceinline__ df &operator-=(df &x, df y) { return x = x - y; }
+__device__ __forceinline__ df &operator*=(df &x, df y) { return x = x * y; }
+__device__ __forceinline__ bool operator<(df x, df y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
+
+// a b + c (a product and a sum, each with its double-word bound)
+__device__ __forceinline__ df fmadd(df a, df b, df c) { return a * b + c; }
+
+// exact multiplication by s = +-1 (the half-turn sign of a lifted rotation)
+__device__ __forceinline__ df sign_mul(df x, df s) { return df(x.hi * s.hi, x.lo * s.hi); }
+
+// transcendental helpers through FP64 (used only off the hot path:
+// imaginary-time factors and large kick angles)
+__device__ __forceinline__ df dexp(df x) { return df(::exp(static_cast<double>(x))); }
+
+}  // namespace ctap

@@ -116,7 +116,7 @@ template <class T>
 __device__ __forceinline__ void kick_one(Cx<T> &v, T th, int imag, int small)
 {
     if (imag) {
-        const T f = exp(-th);
+        const T f = dexp(-th);
         v.x *= f;
         v.y *= f;
     } else {
@@ -166,6 +166,9 @@ __device__ __forceinline__ void st2(double2 *p, const double2 &a, const double2 
     p[0] = a;
     p[1] = b;
 }
+// streaming (evict-first) global access of one complex128 value
+__device__ __forceinline__ double2 ld_stream(const double2 *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream(double2 *p, const double2 &v) { __stcs(p, v); }
 template <int R, class C2> __device__ __forceinline__ void load_pairs(const C2 *p, C2 (&v)[R])
 {
 #pragma unroll
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
             for (int rr = 0; rr < YA; ++rr) {
                 const int y = r + (i + YB * rr) * g.P;
                 const C2 q = ps[(long long)y << g.lgnx];
-                t1 += ((double)vv[rr].x * q.y - (double)vv[rr].y * q.x) * a.gd.g64[y];
+                t1 += ((double)vv[rr].x * (double)q.y - (double)vv[rr].y * (double)q.x) * a.gd.g64[y];
             }
             gacc[0] += t1 * a.gd.D1[(long long)z * g.nx + x];
             gacc[1] += t1 * a.gd.D3[(long long)z * g.nx + x];
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                     for (int rr = 0; rr < YA; ++rr) {
                         const int y = r + (i + YB * rr) * g.P;
                         const C2 u = v[c][rr];
-                        const double d = (double)u.x * u.x + (double)u.y * u.y;
+                        const double d = (double)u.x * (double)u.x + (double)u.y * (double)u.y;
                         double V = 0.0;
                         if (a.vform_obs == VF_DENSE) V = (double)k.Vd[pbase + ((long long)y << g.lgnx) + x];
                         else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * hz + vz64;
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                             const int jy = i + YB * rr;
                             kick_sep<T>(v[c][rr], lx, ytab[jy], lz, k.imag);
                             if (flags & XY_RED_NORM)
-                                acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
+                                acc[0] += (double)v[c][rr].x * (double)v[c][rr].x + (double)v[c][rr].y * (double)v[c][rr].y;
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
                         }
@@ -453,7 +456,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                                     : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
                             kick_one<T>(v[c][rr], th, k.imag, small);
                             if (flags & XY_RED_NORM)
-                                acc[0] += (double)v[c][rr].x * v[c][rr].x + (double)v[c][rr].y * v[c][rr].y;
+                                acc[0] += (double)v[c][rr].x * (double)v[c][rr].x + (double)v[c][rr].y * (double)v[c][rr].y;
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
                         }
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
                         v[i][0][rr] = make_float2(w4.x, w4.y);
                         v[i][1][rr] = make_float2(w4.z, w4.w);
                     } else {
-                        v[i][0][rr] = __ldcs(p + ((long long)rr << g.lgnx));
+                        v[i][0][rr] = ld_stream(p + ((long long)rr << g.lgnx));
                     }
                 }
             }
@@ -714,7 +717,7 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
                     constexpr int k2 = decltype(kc)::value;
                     const C2 u = v[brev(k2, ZB)];
                     acc[0] += (kxy + a.k2h[g.nx + g.ny + jp + ZA * k2]) *
-                              ((double)u.x * u.x + (double)u.y * u.y);
+                              ((double)u.x * (double)u.x + (double)u.y * (double)u.y);
                 });
                 continue;
             }
@@ -794,7 +797,7 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
                 __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
                        make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y));
             else
-                __stcs(p + ((long long)rr << g.lgnx), v[0][rr]);
+                st_stream(p + ((long long)rr << g.lgnx), v[0][rr]);
         }
     }
 }
@@ -1189,6 +1192,11 @@ bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st)
            try_z<float, 512, 32, 16, 2, 16>(a, st) || try_z<float, 256, 16, 16, 4, 16>(a, st) ||
            try_z<float, 256, 16, 16, 2, 32>(a, st) || try_z<float, 256, 16, 16, 1, 64>(a, st);
 }
+
+// The double-float path runs on the generic passes: fully unrolled 32-point
+// register DFTs in double-float arithmetic are too large to compile.
+bool launch_xy_fast(const XYArgs<df> &, cudaStream_t) { return false; }
+bool launch_z_fast(const ZArgs<df> &, cudaStream_t) { return false; }
 
 bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st)
 {

@@ -4,8 +4,6 @@
 
 namespace ctap {
 
-__device__ __forceinline__ float dexp(float x) { return expf(x); }
-__device__ __forceinline__ double dexp(double x) { return exp(x); }
 
 // -------------------------------------------------------------- reductions
 // Block sum of NQ doubles, fixed order (warp shuffles, then warp 0): results
@@ -66,6 +64,18 @@ __device__ __forceinline__ void kick_point(Cx<T> &v, const Kick<T> &k, const Geo
             v.y *= f;
         } else {
             T p, u, s;
+            if constexpr (std::is_same<T, df>::value) {
+                if (fabsf(th.hi) <= 0.1f) {          // double-float series, no FP64
+                    lift_small(th, p, u);
+                    rot_f<T>(v, p, u);
+                    return;
+                }
+                lift_from_angle(-th, p, u, s);
+                rot_f<T>(v, p, u);
+                v.x = sign_mul(v.x, s);
+                v.y = sign_mul(v.y, s);
+                return;
+            }
             lift_from_angle(-th, p, u, s);
             rot_f<T>(v, p, u);
             v.x *= s;
@@ -122,7 +132,7 @@ __global__ void __launch_bounds__(kNT, 1) xy_pass_kernel(const XYArgs<T> a)
     double gacc[2] = {0.0, 0.0};
     auto grad_point = [&](const Cx<T> &v, int x, int y) {
         const Cx<T> q = static_cast<const Cx<T> *>(a.gd.psi)[pbase + ((long long)y << g.lgnx) + x];
-        const double im = ((double)v.x * q.y - (double)v.y * q.x) * a.gd.g64[y];
+        const double im = ((double)v.x * (double)q.y - (double)v.y * (double)q.x) * a.gd.g64[y];
         gacc[0] += im * a.gd.D1[(long long)z * g.nx + x];
         gacc[1] += im * a.gd.D3[(long long)z * g.nx + x];
     };
@@ -373,6 +383,53 @@ __global__ void density_xz_kernel(const Cx<T> *psi, const Geom g, double dy, dou
     out[i] = acc * dy;
 }
 
+// ------------------------------------- complex128 <-> double-float storage
+// In place: a complex128 value and its double-float form both take 16 bytes.
+__global__ void c128_to_df_kernel(double2 *p, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = p[i];
+        df2 w;
+        w.x = df(v.x);
+        w.y = df(v.y);
+        reinterpret_cast<df2 *>(p)[i] = w;
+    }
+}
+__global__ void df_to_c128_kernel(double2 *p, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const df2 w = reinterpret_cast<const df2 *>(p)[i];
+        p[i] = make_double2(static_cast<double>(w.x), static_cast<double>(w.y));
+    }
+}
+__global__ void c128_to_df_copy_kernel(const double2 *src, df2 *dst, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        df2 w;
+        w.x = df(v.x);
+        w.y = df(v.y);
+        dst[i] = w;
+    }
+}
+
+void launch_c128_to_df(void *psi, long long n, cudaStream_t st)
+{
+    c128_to_df_kernel<<<1184, 256, 0, st>>>(static_cast<double2 *>(psi), n);
+}
+void launch_df_to_c128(void *psi, long long n, cudaStream_t st)
+{
+    df_to_c128_kernel<<<1184, 256, 0, st>>>(static_cast<double2 *>(psi), n);
+}
+void launch_c128_to_df_copy(const void *src, void *dst, long long n, cudaStream_t st)
+{
+    c128_to_df_copy_kernel<<<1184, 256, 0, st>>>(static_cast<const double2 *>(src),
+                                                 static_cast<df2 *>(dst), n);
+}
+
 // -------------------------------------------------------------- launchers
 int xy_grid(const Geom &g) { return g.batch * g.nz * g.P; }
 int z_grid(const Geom &g) { return g.batch << g.lgzt; }
@@ -445,6 +502,9 @@ void launch_density_xz(const Cx<T> *psi, const Geom &g, double dy, double *out, 
 
 template void launch_density_xz<float>(const Cx<float> *, const Geom &, double, double *, cudaStream_t);
 template void launch_density_xz<double>(const Cx<double> *, const Geom &, double, double *, cudaStream_t);
+template void launch_xy<df>(const XYArgs<df> &, cudaStream_t);
+template void launch_z<df>(const ZArgs<df> &, cudaStream_t);
+template void launch_scale<df>(Cx<df> *, long long, const double *, cudaStream_t);
 template void launch_xy<float>(const XYArgs<float> &, cudaStream_t);
 template void launch_xy<double>(const XYArgs<double> &, cudaStream_t);
 template void launch_z<float>(const ZArgs<float> &, cudaStream_t);

@@ -156,7 +156,15 @@ bool fast_xy_supported(int esize, int nx, int Ly);
 bool fast_z_supported(int esize, int nz, int P, int w);
 bool launch_xy_fast(const XYArgs<float> &a, cudaStream_t st);
 bool launch_xy_fast(const XYArgs<double> &a, cudaStream_t st);
+bool launch_xy_fast(const XYArgs<df> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st);
+bool launch_z_fast(const ZArgs<df> &a, cudaStream_t st);
+
+// complex128 psi <-> double-float storage (n complex values), in place or
+// into a separate buffer
+void launch_c128_to_df(void *psi, long long n, cudaStream_t st);
+void launch_df_to_c128(void *psi, long long n, cudaStream_t st);
+void launch_c128_to_df_copy(const void *src, void *dst, long long n, cudaStream_t st);
 
 }  // namespace ctap

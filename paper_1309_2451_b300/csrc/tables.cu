@@ -60,12 +60,14 @@ static void put_any(const PlanState &st, std::vector<unsigned char> &h, size_t i
                     double u, double s, double f)
 {
     if (st.dtype == CTAP_C64) put<float>(h, idx, p, u, s, f);
+    else if (st.dtype == CTAP_C128_DF) put<df>(h, idx, p, u, s, f);
     else put<double>(h, idx, p, u, s, f);
 }
 
 static size_t lift_size(const PlanState &st)
 {
-    return st.dtype == CTAP_C64 ? sizeof(Lift<float>) : sizeof(Lift<double>);
+    if (st.dtype == CTAP_C64) return sizeof(Lift<float>);
+    return st.dtype == CTAP_C128_DF ? sizeof(Lift<df>) : sizeof(Lift<double>);
 }
 
 static AxisPlan make_axis(int L, int maxv, int &table_entries)

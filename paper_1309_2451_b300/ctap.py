@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libctap.so")
 
-CTAP_C64, CTAP_C128 = 0, 1
+CTAP_C64, CTAP_C128, CTAP_C128_DF = 0, 1, 2
 CTAP_REAL, CTAP_IMAG, CTAP_REAL_KVK = 0, 1, 2
 STATUS = ["ok", "invalid argument", "unsupported size", "dtype mismatch", "no potential",
           "out of memory", "CUDA error", "timeout", "non-finite result"]
@@ -113,7 +113,8 @@ class Plan:
         self.batch = int(batch)
         self.psi_shape = self.shape if self.batch == 1 else (self.batch,) + self.shape
         self.box = tuple(float(b) for b in box)
-        self.dtype = {"c64": CTAP_C64, "c128": CTAP_C128,
+        # "c128df": complex128 psi, transforms in double-float (FP32-pair) arithmetic
+        self.dtype = {"c64": CTAP_C64, "c128": CTAP_C128, "c128df": CTAP_C128_DF,
                       torch.complex64: CTAP_C64, torch.complex128: CTAP_C128}[dtype]
         self.torch_dtype = torch.complex64 if self.dtype == CTAP_C64 else torch.complex128
         if stream is None:

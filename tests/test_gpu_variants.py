@@ -246,3 +246,61 @@ def test_batched_plan_restrictions(ctap):
     assert e.value.code == 1
     with pytest.raises(ValueError):
         plan.step(to_dev(np.zeros(shape, complex), "c64"), 1, 0.01)
+
+
+# ---------------------------------------- double-float complex128 path (N1)
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 32, 16), (256, 64, 64)])
+def test_double_float_path_matches_oracle(ctap, shape):
+    """Complex128 psi with double-float transforms: harmonic oscillator,
+    100 steps (the complex128 target is 1e-12 relative L2)."""
+    box = (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
+    vx, vy, vz = wl.harmonic_parts(shape, box)
+    psi0 = wl.gaussian_sum(shape, box, seed=40)
+    plan = ctap.Plan(shape, box, "c128df")
+    plan.set_potential(wl.harmonic_dense(shape, box))
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 100, 0.005)
+    ref = oracle.step(psi0, wl.harmonic_dense(shape, box), box, 0.005, 100)
+    err = rel(psi.cpu().numpy(), ref)
+    assert err < 1e-12, err
+    # far better than complex64 on the same run
+    p64 = ctap.Plan(shape, box, "c64")
+    p64.set_potential(wl.harmonic_dense(shape, box))
+    q = to_dev(psi0, "c64")
+    p64.step(q, 100, 0.005)
+    assert rel(q.cpu().numpy().astype(complex), ref) > 100 * err
+
+
+@pytest.mark.parametrize("order", ["VKV", "KVK"])
+def test_double_float_guides_and_observables(ctap, order):
+    shape, box = (256, 64, 64), wl.CTAP_BOX
+    plan, V, c = guides(ctap, shape, box, "c128df", trap=wl.TRAP_OMEGA)
+    psi0 = guide_state(shape, box, 41)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 20, 0.0025, order=order)
+    ref = oracle.step(psi0, V, box, 0.0025, 20, order=order)
+    assert rel(psi.cpu().numpy(), ref) < 1e-12
+    got = plan.observables(psi)
+    want = oracle.observables(ref, V, box, c, wl.POP_HALFWIDTH)
+    assert np.allclose(got, want, rtol=1e-11, atol=1e-14)
+
+
+def test_double_float_imaginary_time(ctap):
+    shape, box = (32, 32, 32), (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
+    vx, vy, vz = wl.harmonic_parts(shape, box)
+    plan = ctap.Plan(shape, box, "c128df")
+    plan.set_potential_separable(vx, vy, vz)
+    psi0 = wl.gaussian_sum(shape, box, seed=42)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 20, 0.02, imag=True)
+    ref = oracle.step(psi0, wl.harmonic_dense(shape, box), box, 0.02, 20, imag=True)
+    assert rel(psi.cpu().numpy(), ref) < 1e-12
+
+
+def test_double_float_adjoint_is_rejected(ctap):
+    shape, box = (16, 16, 16), wl.CTAP_BOX
+    plan = ctap.Plan(shape, box, "c128df")
+    plan.set_guides_spline(wl.V0, wl.SIGMA_GUIDE, wl.KNOTS_Z, *wl.spline_controls())
+    with pytest.raises(ctap.CtapError) as e:
+        plan.adjoint(to_dev(np.zeros(shape, complex), "c128"), 4, 0.01)
+    assert e.value.code == 3
