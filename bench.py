@@ -260,6 +260,16 @@ def time_variants(torch, wl, device, stream, plan, psi, reps=4):
         plan.density_xz(psi)
     out["density_xz"] = {"ms_per_call_with_copy": 1000.0 * (time.perf_counter() - t0) / reps,
                          "bytes_read": int(np.prod(SHAPE)) * 8}
+    # atom-chip potential from 3 x 64 wire segments on the full grid (device
+    # FP64 Biot-Savart sum, then stored as the dense form)
+    from paper_1309_2451_b300 import ctap
+    chip = ctap.Plan(SHAPE, (-10.0, 10.0, 0.5, 4.5, 0.0, 1000.0), "c64", stream=stream)
+    seg = wl.chip_wires(64)
+    t0 = time.perf_counter()
+    chip.set_potential_wires(seg, wl.chip_bias(), wl.CHIP["mu0_over_4pi"], 0.5, 0.5 * wl.CHIP["B_ip"])
+    out["wire_potential_build"] = {"s": time.perf_counter() - t0, "segments": int(seg.shape[0]),
+                                   "points": int(np.prod(SHAPE))}
+    chip.close()
     return out
 
 

@@ -102,6 +102,21 @@ ctap_status ctap_plan_destroy(ctap_plan_t plan);
  * precision (FP32 for CTAP_C64, FP64 for CTAP_C128). */
 ctap_status ctap_set_potential(ctap_plan_t plan, const double *V);
 
+/* Potential of an atom chip (Sec. III): thin straight current-carrying wire
+ * segments (the Biot-Savart law, Eq. 4) plus a uniform field (the bias field
+ * that lifts the minimum above the wires, Eq. 5, and the field along the
+ * wires), V = v_per_field |B| - v_offset, evaluated on the device in FP64
+ * and stored in the general (dense) form.  seg: host FP64 [nseg][7] rows
+ * (Ax, Ay, Az, Cx, Cy, Cz, I) in grid units, current I from A to C;
+ * bias: host FP64 [3]; mu0_over_4pi: the Biot-Savart constant in the
+ * caller's units (field per current, times length); v_per_field converts
+ * |B| to the plan's energy unit.  A grid point on a segment's line gets no
+ * field from that segment.  nseg in [1, CTAP_MAX_SEGMENTS]; batch == 1. */
+#define CTAP_MAX_SEGMENTS 65536
+ctap_status ctap_set_potential_wires(ctap_plan_t plan, int nseg, const double *seg,
+                                     const double *bias, double mu0_over_4pi,
+                                     double v_per_field, double v_offset);
+
 /* Potential, additively separable form V = Vx(x) + Vy(y) + Vz(z)
  * (e.g. the harmonic trap): three host FP64 arrays of nx, ny, nz values.
  * Phase factors are generated per axis in FP64 on the host. */

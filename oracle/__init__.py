@@ -50,6 +50,8 @@ def _load():
         lib.orc_adjoint.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
                                     ctypes.c_double, ctypes.c_int, _dp, _dp, _dp,
                                     _dp, _dp, _dp]
+        lib.orc_wire_field.argtypes = [_dp, ctypes.c_long, ctypes.c_int, _dp, _dp,
+                                       ctypes.c_double, _dp]
         lib.orc_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -188,6 +190,32 @@ def ctap_potential(shape, box, V0, s, x1z, x3z):
     _check(_load().orc_ctap_potential(_ptr(V), nx, ny, nz, _ptr(_box(box)), float(V0), float(s),
                                       _ptr(_f64(x1z)), _ptr(_f64(x3z))), "ctap_potential")
     return V
+
+
+def wire_field(points, segments, bias, k):
+    """Magnetic field of thin straight current segments plus a uniform field
+    (Sec. III, Eq. 4-5) at points (n, 3): segments (m, 7) rows
+    (Ax, Ay, Az, Cx, Cy, Cz, I), bias (3,), k = mu0/(4 pi) in the caller's
+    units.  Returns (n, 3)."""
+    P = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    S = np.ascontiguousarray(segments, dtype=np.float64).reshape(-1, 7)
+    out = np.zeros_like(P)
+    _check(_load().orc_wire_field(_ptr(P), P.shape[0], S.shape[0], _ptr(S), _ptr(_f64(bias)),
+                                  float(k), _ptr(out)), "wire_field")
+    return out
+
+
+def wire_potential(shape, box, segments, bias, k, v_per_field, v_offset=0.0):
+    """Magnetic trapping potential V = v_per_field |B| - v_offset on the grid
+    (Sec. III: the atom-chip waveguides)."""
+    nz, ny, nx = shape
+    x = grid_axis(nx, box[0], box[1])
+    y = grid_axis(ny, box[2], box[3])
+    z = grid_axis(nz, box[4], box[5])
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    B = wire_field(pts, segments, bias, k)
+    return (v_per_field * np.sqrt((B * B).sum(axis=1)) - v_offset).reshape(shape)
 
 
 def ctap_dvdx(shape, box, V0, s, xjz):

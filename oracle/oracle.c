@@ -326,6 +326,59 @@ int orc_observables(const double *psi, const double *V, int nx, int ny, int nz,
  * with x_1 = x1z[z], x_2 = 0, x_3 = x3z[z]: three parallel Gaussian
  * waveguides whose separations vary along z (the spatial form of the
  * time-dependent couplings of Eq. (1)). */
+/* ------------------------------------------------------ atom-chip wires */
+
+/* Magnetic field of thin straight current segments plus a uniform field
+ * (Sec. III, Eq. 4: the Biot-Savart law; a homogeneous bias field lifts the
+ * minimum above the wire, Eq. 5, and a field along the wires removes the
+ * zero).  For one straight segment from A to C carrying I, the line integral
+ * of Eq. 4 evaluates in closed form: at perpendicular distance d from the
+ * line through A and C,
+ *     |B| = k I (cos t1 - cos t2) / d,   k = mu0 / (4 pi),
+ * where t1, t2 are the angles between the direction A->C and the vectors
+ * from A and from C to the point, and B points along (C - A) x (P - A).
+ * seg[7 m .. 7 m + 6] = (Ax, Ay, Az, Cx, Cy, Cz, I); pts[3 i ..] the points;
+ * B[3 i ..] receives bias + the sum over segments (segments in input
+ * order).  A point on a segment's line (d = 0) gets no contribution from
+ * that segment. */
+int orc_wire_field(const double *pts, long npts, int nseg, const double *seg,
+                   const double *bias, double k, double *B)
+{
+    #pragma omp parallel for schedule(static)
+    for (long i = 0; i < npts; ++i) {
+        const double *P = pts + 3 * i;
+        double b[3] = {bias[0], bias[1], bias[2]};
+        for (int m = 0; m < nseg; ++m) {
+            const double *A = seg + 7 * m, *C = A + 3;
+            const double cur = A[6];
+            double t[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+            const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+            if (len == 0.0) continue;
+            for (int q = 0; q < 3; ++q) t[q] /= len;
+            const double pa[3] = {P[0] - A[0], P[1] - A[1], P[2] - A[2]};
+            const double pc[3] = {P[0] - C[0], P[1] - C[1], P[2] - C[2]};
+            const double along = pa[0] * t[0] + pa[1] * t[1] + pa[2] * t[2];
+            double perp[3] = {pa[0] - along * t[0], pa[1] - along * t[1], pa[2] - along * t[2]};
+            const double d = sqrt(perp[0] * perp[0] + perp[1] * perp[1] + perp[2] * perp[2]);
+            if (d == 0.0) continue;
+            const double ra = sqrt(pa[0] * pa[0] + pa[1] * pa[1] + pa[2] * pa[2]);
+            const double rc = sqrt(pc[0] * pc[0] + pc[1] * pc[1] + pc[2] * pc[2]);
+            const double cos1 = along / ra;
+            const double cos2 = (pc[0] * t[0] + pc[1] * t[1] + pc[2] * t[2]) / rc;
+            const double mag = k * cur * (cos1 - cos2) / d;
+            /* direction: t x perp / d */
+            const double n[3] = {(t[1] * perp[2] - t[2] * perp[1]) / d,
+                                 (t[2] * perp[0] - t[0] * perp[2]) / d,
+                                 (t[0] * perp[1] - t[1] * perp[0]) / d};
+            for (int q = 0; q < 3; ++q) b[q] += mag * n[q];
+        }
+        B[3 * i] = b[0];
+        B[3 * i + 1] = b[1];
+        B[3 * i + 2] = b[2];
+    }
+    return 0;
+}
+
 int orc_ctap_potential(double *V, int nx, int ny, int nz, const double *box,
                        double V0, double s, const double *x1z, const double *x3z)
 {

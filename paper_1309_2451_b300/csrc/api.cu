@@ -904,6 +904,45 @@ ctap_status ctap_set_potential(ctap_plan_t plan, const double *V)
     return CTAP_OK;
 }
 
+ctap_status ctap_set_potential_wires(ctap_plan_t plan, int nseg, const double *seg,
+                                     const double *bias, double mu0_over_4pi, double v_per_field,
+                                     double v_offset)
+{
+    PlanState *st = S(plan);
+    if (!st || nseg < 1 || nseg > CTAP_MAX_SEGMENTS || !seg || !bias) return CTAP_ERR_INVALID_ARG;
+    if (st->batch > 1) return fail(*st, CTAP_ERR_INVALID_ARG, "batched plans take the product form");
+    for (int i = 0; i < 7 * nseg; ++i)
+        if (!std::isfinite(seg[i])) return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite segment");
+    if (!std::isfinite(bias[0]) || !std::isfinite(bias[1]) || !std::isfinite(bias[2]) ||
+        !std::isfinite(mu0_over_4pi) || !std::isfinite(v_per_field) || !std::isfinite(v_offset))
+        return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite field parameter");
+    void *dseg = nullptr, *dV = nullptr;
+    CTAP_TRY(dev_alloc(*st, &dseg, sizeof(double) * 7 * nseg));
+    ctap_status rc = dev_alloc(*st, &dV, sizeof(double) * st->N);
+    if (rc != CTAP_OK) {
+        dev_free(dseg);
+        return rc;
+    }
+    std::vector<double> V(st->N);
+    cudaError_t e = cudaMemcpyAsync(dseg, seg, sizeof(double) * 7 * nseg, cudaMemcpyHostToDevice,
+                                    st->stream);
+    if (e == cudaSuccess) {
+        rc = go_other(*st, "wire field", [&] {
+            launch_wire_potential(static_cast<double *>(dV), st->geom, static_cast<double *>(dseg),
+                                  nseg, bias, mu0_over_4pi, v_per_field, v_offset, st->stream);
+        });
+        if (rc == CTAP_OK)
+            e = cudaMemcpyAsync(V.data(), dV, sizeof(double) * st->N, cudaMemcpyDeviceToHost,
+                                st->stream);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(*st, e, "wire field");
+    if (rc == CTAP_OK) rc = wait_stream(*st, 0);
+    dev_free(dseg);
+    dev_free(dV);
+    if (rc != CTAP_OK) return rc;
+    return ctap_set_potential(plan, V.data());      // dense form, plan precision
+}
+
 ctap_status ctap_set_potential_separable(ctap_plan_t plan, const double *Vx, const double *Vy,
                                          const double *Vz)
 {

@@ -383,6 +383,53 @@ __global__ void density_xz_kernel(const Cx<T> *psi, const Geom g, double dy, dou
     out[i] = acc * dy;
 }
 
+// ------------------------------------------------- atom-chip wire field
+// V = vs |B| - voff on the grid, B = bias + the Biot-Savart field of thin
+// straight segments (Sec. III, Eq. 4): for a segment A -> C carrying I, at P
+// with a = P - A, c = P - C, l = C - A,
+//     B = k I (l x a) / |l x a|^2 (l.a/|a| - l.c/|c|),   k = mu0/(4 pi).
+// One thread per grid point, segments summed in input order (FP64).
+__global__ void wire_potential_kernel(double *V, const Geom g, const double *seg, int nseg,
+                                      double bx, double by, double bz, double k, double vs,
+                                      double voff)
+{
+    const long long n = g.plane * g.nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i & (g.nx - 1));
+        const int y = (int)((i >> g.lgnx) & (g.ny - 1));
+        const int z = (int)(i >> (g.lgnx + g.lgny));
+        const double px = g.box[0] + x * (g.box[1] - g.box[0]) / g.nx;
+        const double py = g.box[2] + y * (g.box[3] - g.box[2]) / g.ny;
+        const double pz = g.box[4] + z * (g.box[5] - g.box[4]) / g.nz;
+        double b0 = bx, b1 = by, b2 = bz;
+        for (int m = 0; m < nseg; ++m) {
+            const double *s = seg + 7 * m;
+            const double lx = s[3] - s[0], ly = s[4] - s[1], lz = s[5] - s[2];
+            const double ax = px - s[0], ay = py - s[1], az = pz - s[2];
+            const double cx = px - s[3], cy = py - s[4], cz = pz - s[5];
+            const double nx_ = ly * az - lz * ay, ny_ = lz * ax - lx * az, nz_ = lx * ay - ly * ax;
+            const double n2 = nx_ * nx_ + ny_ * ny_ + nz_ * nz_;
+            if (n2 == 0.0) continue;                        // on the segment's line
+            const double ra = sqrt(ax * ax + ay * ay + az * az);
+            const double rc = sqrt(cx * cx + cy * cy + cz * cz);
+            const double f = k * s[6] * ((lx * ax + ly * ay + lz * az) / ra -
+                                         (lx * cx + ly * cy + lz * cz) / rc) / n2;
+            b0 += f * nx_;
+            b1 += f * ny_;
+            b2 += f * nz_;
+        }
+        V[i] = vs * sqrt(b0 * b0 + b1 * b1 + b2 * b2) - voff;
+    }
+}
+
+void launch_wire_potential(double *V, const Geom &g, const double *seg, int nseg,
+                           const double bias[3], double k, double vs, double voff, cudaStream_t st)
+{
+    wire_potential_kernel<<<148 * 8, 256, 0, st>>>(V, g, seg, nseg, bias[0], bias[1], bias[2], k,
+                                                   vs, voff);
+}
+
 // ------------------------------------- complex128 <-> double-float storage
 // In place: a complex128 value and its double-float form both take 16 bytes.
 __global__ void c128_to_df_kernel(double2 *p, long long n)

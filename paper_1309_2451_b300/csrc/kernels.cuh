@@ -161,6 +161,12 @@ bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<df> &a, cudaStream_t st);
 
+// V = vs |B| - voff on the grid ([nz][ny][nx], FP64, device) from thin
+// current segments seg[7 m ..] = (A, C, I) and a uniform field bias
+void launch_wire_potential(double *V, const Geom &g, const double *seg, int nseg,
+                           const double bias[3], double k, double vs, double voff,
+                           cudaStream_t st);
+
 // complex128 psi <-> double-float storage (n complex values), in place or
 // into a separate buffer
 void launch_c128_to_df(void *psi, long long n, cudaStream_t st);

@@ -43,6 +43,7 @@ def lib():
         "ctap_plan_create": [i, i, i, _dp, i, _vp, ctypes.POINTER(_vp)],
         "ctap_plan_create_batched": [i, i, i, i, _dp, i, _vp, ctypes.POINTER(_vp)],
         "ctap_set_guides_batched": [_vp, d, d, _dp, _dp, _dp, d, i],
+        "ctap_set_potential_wires": [_vp, i, _dp, _dp, d, d, d],
         "ctap_plan_destroy": [_vp],
         "ctap_set_potential": [_vp, _dp],
         "ctap_set_potential_separable": [_vp, _dp, _dp, _dp],
@@ -84,7 +85,8 @@ def exported_symbols():
             "ctap_adjoint", "ctap_sync", "ctap_set_timeout", "ctap_launch_count",
             "ctap_set_profiling", "ctap_pass_times", "ctap_plan_info", "ctap_status_string",
             "ctap_last_error", "ctap_version", "ctap_norm_noalloc", "ctap_add_potential_z",
-            "ctap_density_xz", "ctap_plan_create_batched", "ctap_set_guides_batched"]
+            "ctap_density_xz", "ctap_plan_create_batched", "ctap_set_guides_batched",
+            "ctap_set_potential_wires"]
 
 
 def _f64(a, n=None):
@@ -159,6 +161,16 @@ class Plan:
     # ----------------------------------------------------------- potential
     def set_potential(self, V):
         self._check(lib().ctap_set_potential(self._h, _p(_f64(V, int(np.prod(self.psi_shape))))))
+
+    def set_potential_wires(self, segments, bias, mu0_over_4pi, v_per_field, v_offset=0.0):
+        """Atom-chip potential v_per_field |B| - v_offset from thin wire
+        segments (rows A, C, I) and a uniform field (Sec. III, Eq. 4-5)."""
+        seg = _f64(segments)
+        if seg.size % 7:
+            raise ValueError("segments must have 7 values per row")
+        self._check(lib().ctap_set_potential_wires(self._h, seg.size // 7, _p(seg),
+                                                   _p(_f64(bias, 3)), float(mu0_over_4pi),
+                                                   float(v_per_field), float(v_offset)))
 
     def set_potential_separable(self, Vx, Vy, Vz):
         nz, ny, nx = self.shape

@@ -92,6 +92,45 @@ def guide_centres(z, order="counter"):
     return np.stack([-separation(z, zc12), np.zeros_like(z), separation(z, zc23)])
 
 
+# Atom-chip wires (Sec. III, Fig. 1-3 captions): lengths in um, fields in
+# gauss, currents in A.  mu0/(4 pi) = 1e-7 T m/A = 1e3 G um/A.
+CHIP = dict(mu0_over_4pi=1.0e3, I_outer=0.1, I_mid=0.07, B_bias=140.0, B_ip=300.0,
+            sep_far=7.0, sep_near=4.3, straight=50.0, length=1000.0, width=12.0)
+
+
+def chip_wires(nseg=64, order="counter", zc=(600.0, 400.0), w=120.0, **kw):
+    """Three wires on the chip surface (the plane y = 0) running along z over
+    the chip length: polylines of nseg straight segments each, rows
+    (Ax, Ay, Az, Cx, Cy, Cz, I).  The gaps to the middle wire shrink from
+    sep_far to sep_near as Gaussian dips centred at zc = (left, right); the
+    left wire stays straight over the first `straight` um (the asymmetry of
+    Fig. 2).  The paper gives these numbers but not the wire curves: the dip
+    profile is this stand-in's choice.  order "intuitive" exchanges the two
+    dips."""
+    c = dict(CHIP, **kw)
+    zl, zr = zc if order == "counter" else zc[::-1]
+    z = np.linspace(0.0, c["length"], nseg + 1)
+
+    def gap(zz, z0):
+        return c["sep_far"] - (c["sep_far"] - c["sep_near"]) * np.exp(-(zz - z0) ** 2 / (2 * w * w))
+
+    xl = -gap(z, zl)
+    xl[z <= c["straight"]] = -c["sep_far"]
+    xr = gap(z, zr)
+    rows = []
+    for xs, cur in ((xl, c["I_outer"]), (np.zeros_like(z), c["I_mid"]), (xr, c["I_outer"])):
+        for i in range(nseg):
+            rows.append([xs[i], 0.0, z[i], xs[i + 1], 0.0, z[i + 1], cur])
+    return np.array(rows)
+
+
+def chip_bias(**kw):
+    """Uniform field: the bias along x (in the chip plane, across the wires)
+    and the field along the wires (z)."""
+    c = dict(CHIP, **kw)
+    return np.array([c["B_bias"], 0.0, c["B_ip"]])
+
+
 def trap_z(z, omega=TRAP_OMEGA, zc=0.0):
     """Longitudinal harmonic trap omega^2 (z - zc)^2 / 2 centred on the chip
     (Sec. III: it accelerates the atom along the guides and refocuses it at

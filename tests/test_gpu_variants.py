@@ -304,3 +304,35 @@ def test_double_float_adjoint_is_rejected(ctap):
     with pytest.raises(ctap.CtapError) as e:
         plan.adjoint(to_dev(np.zeros(shape, complex), "c128"), 4, 0.01)
     assert e.value.code == 3
+
+
+# --------------------------------------------- atom-chip wire potential (N4)
+@pytest.mark.parametrize("shape", [(64, 32, 64), (128, 16, 32)])
+def test_wire_potential_matches_oracle(ctap, shape):
+    """Biot-Savart field of the three chip wires plus the bias fields, built
+    on the device, against the oracle; then steps on it (complex128)."""
+    box = (-10.0, 10.0, 0.5, 4.5, 0.0, 1000.0)
+    seg = wl.chip_wires(48)
+    bias = wl.chip_bias()
+    k = wl.CHIP["mu0_over_4pi"]
+    vpf, voff = 0.5, 0.5 * wl.CHIP["B_ip"]
+    plan = ctap.Plan(shape, box, "c128")
+    plan.set_potential_wires(seg, bias, k, vpf, voff)
+    got = plan.get_potential()
+    want = oracle.wire_potential(shape, box, seg, bias, k, vpf, voff)
+    assert rel(got, want) < 1e-13
+    x, y, z = wl.mesh(shape, box)
+    psi0 = wl.normalise(np.exp(-x ** 2 / 8.0 - (y - 2.5) ** 2 / 1.0 - (z - 500.0) ** 2 / 7200.0
+                               + 0.05j * z), box)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 5, 0.01)
+    assert rel(psi.cpu().numpy(), oracle.step(psi0, want, box, 0.01, 5)) < 1e-12
+
+
+def test_wire_potential_rejects_bad_input(ctap):
+    plan = ctap.Plan((8, 8, 8), (-1, 1, -1, 1, -1, 1), "c64")
+    with pytest.raises(ctap.CtapError) as e:
+        plan.set_potential_wires(np.full((1, 7), np.nan), [0, 0, 0], 1.0, 1.0)
+    assert e.value.code == 1
+    with pytest.raises(ValueError):
+        plan.set_potential_wires(np.zeros(6), [0, 0, 0], 1.0, 1.0)
