@@ -828,7 +828,7 @@ ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const do
     const int maxv = dtype == CTAP_C64 ? 32 : 16;
     const int emax = kNT * maxv;
     const char *fg = std::getenv("CTAP_FORCE_GENERIC");
-    st.force_generic = (fg && fg[0] == '1') || dtype == CTAP_C128_DF;   // double-float: generic passes
+    st.force_generic = fg && fg[0] == '1';
     const char *nr = std::getenv("CTAP_NO_RING");
     st.no_ring = nr && nr[0] == '1';
     try {
@@ -836,6 +836,10 @@ ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const do
     } catch (const std::exception &) {
         delete p;
         return CTAP_ERR_UNSUPPORTED_SIZE;
+    }
+    if (dtype == CTAP_C128_DF) {          // double-float: specialised XY pass for nx = 256 only
+        st.fast_xy = st.fast_xy && nx == 256;
+        st.fast_z = false;
     }
     auto bail = [&](ctap_status s) {
         ctap_plan_destroy(p);

@@ -112,6 +112,32 @@ __device__ __forceinline__ void kick_rt(double2 &v, double th, int small)
     v.y *= s;
 }
 
+// double-float kick: the double-float series for |th| <= 0.1, the FP64
+// reduction otherwise
+__device__ __forceinline__ void kick_rt(df2 &v, df th, int small)
+{
+    df p, u, s;
+    if (small && fabsf(th.hi) <= 0.1f) {
+        lift_small(th, p, u);
+        rot_f<df>(v, p, u);
+        return;
+    }
+    lift_from_angle(-th, p, u, s);
+    rot_f<df>(v, p, u);
+    v.x = sign_mul(v.x, s);
+    v.y = sign_mul(v.y, s);
+}
+__device__ __forceinline__ void ld2(const df2 *p, df2 &a, df2 &b)
+{
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void st2(df2 *p, const df2 &a, const df2 &b)
+{
+    p[0] = a;
+    p[1] = b;
+}
+
 template <class T>
 __device__ __forceinline__ void kick_one(Cx<T> &v, T th, int imag, int small)
 {
@@ -1193,9 +1219,13 @@ bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st)
            try_z<float, 256, 16, 16, 2, 32>(a, st) || try_z<float, 256, 16, 16, 1, 64>(a, st);
 }
 
-// The double-float path runs on the generic passes: fully unrolled 32-point
-// register DFTs in double-float arithmetic are too large to compile.
-bool launch_xy_fast(const XYArgs<df> &, cudaStream_t) { return false; }
+// Double-float: the specialised XY pass for 256-point rows (16-point
+// register DFTs); the Z pass runs on the generic kernel (fully unrolled
+// 32-point register DFTs in double-float arithmetic are too large to compile).
+bool launch_xy_fast(const XYArgs<df> &a, cudaStream_t st)
+{
+    return try_xy<df, 256, 16, 16, 32, 4, 8>(a, st);
+}
 bool launch_z_fast(const ZArgs<df> &, cudaStream_t) { return false; }
 
 bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st)
