@@ -138,6 +138,10 @@ __device__ __forceinline__ void st2(df2 *p, const df2 &a, const df2 &b)
     p[1] = b;
 }
 
+__device__ __forceinline__ float norm2(const float2 &v) { return fmadd(v.x, v.x, v.y * v.y); }
+__device__ __forceinline__ double norm2(const double2 &v) { return fmadd(v.x, v.x, v.y * v.y); }
+__device__ __forceinline__ df norm2(const df2 &v) { return v.x * v.x + v.y * v.y; }
+
 template <class T>
 __device__ __forceinline__ void kick_one(Cx<T> &v, T th, int imag, int small)
 {
@@ -387,11 +391,22 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
         auto grad_task = [&](const C2 (&vv)[YA], int i, int x) {
             const C2 *ps = static_cast<const C2 *>(a.gd.psi) + pbase + x;
             double t1 = 0.0;
+            if constexpr (std::is_same<T, float>::value) {
+                float tf = 0.0f;                // the column's partial in FP32 (complex64 data)
 #pragma unroll
-            for (int rr = 0; rr < YA; ++rr) {
-                const int y = r + (i + YB * rr) * g.P;
-                const C2 q = ps[(long long)y << g.lgnx];
-                t1 += ((double)vv[rr].x * (double)q.y - (double)vv[rr].y * (double)q.x) * a.gd.g64[y];
+                for (int rr = 0; rr < YA; ++rr) {
+                    const int y = r + (i + YB * rr) * g.P;
+                    const C2 q = ps[(long long)y << g.lgnx];
+                    tf = fmadd(fmadd(vv[rr].x, q.y, -vv[rr].y * q.x), (float)a.gd.g64[y], tf);
+                }
+                t1 = tf;
+            } else {
+#pragma unroll
+                for (int rr = 0; rr < YA; ++rr) {
+                    const int y = r + (i + YB * rr) * g.P;
+                    const C2 q = ps[(long long)y << g.lgnx];
+                    t1 += ((double)vv[rr].x * (double)q.y - (double)vv[rr].y * (double)q.x) * a.gd.g64[y];
+                }
             }
             gacc[0] += t1 * a.gd.D1[(long long)z * g.nx + x];
             gacc[1] += t1 * a.gd.D3[(long long)z * g.nx + x];
@@ -427,20 +442,44 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                     const double vz64 = a.rd.vz64 ? a.rd.vz64[zl] : 0.0;
                     const double vxz = (a.vform_obs == VF_SEPARABLE)
                                            ? a.rd.Vsep[x] + a.rd.Vsep[g.nx + g.ny + zl] : 0.0;
+                    if constexpr (std::is_same<T, float>::value) {
+                        // complex64: products and the column's YA-term partial sums in
+                        // FP32 (the data carry 24 bits), FP64 from there on; FP64
+                        // arithmetic per point would bind this pass to B300's FP64 rate
+                        float sd = 0.0f, svd = 0.0f;
 #pragma unroll
-                    for (int rr = 0; rr < YA; ++rr) {
-                        const int y = r + (i + YB * rr) * g.P;
-                        const C2 u = v[c][rr];
-                        const double d = (double)u.x * (double)u.x + (double)u.y * (double)u.y;
-                        double V = 0.0;
-                        if (a.vform_obs == VF_DENSE) V = (double)k.Vd[pbase + ((long long)y << g.lgnx) + x];
-                        else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * hz + vz64;
-                        else if (a.vform_obs == VF_SEPARABLE) V = vxz + a.rd.Vsep[g.nx + y];
-                        acc[0] += d;
-                        acc[1] += V * d;
-                        acc[2] += in0 ? d : 0.0;
-                        acc[3] += in1 ? d : 0.0;
-                        acc[4] += in2 ? d : 0.0;
+                        for (int rr = 0; rr < YA; ++rr) {
+                            const int jy = i + YB * rr, y = r + jy * g.P;
+                            const C2 u = v[c][rr];
+                            const float d = fmadd(u.x, u.x, u.y * u.y);
+                            float V = 0.0f;
+                            if (a.vform_obs == VF_DENSE) V = k.Vd[pbase + ((long long)y << g.lgnx) + x];
+                            else if (a.vform_obs == VF_PRODUCT) V = (float)a.rd.g64[y] * (float)hz + (float)vz64;
+                            else if (a.vform_obs == VF_SEPARABLE) V = (float)(vxz + a.rd.Vsep[g.nx + y]);
+                            sd += d;
+                            svd = fmadd(V, d, svd);
+                        }
+                        acc[0] += sd;
+                        acc[1] += svd;
+                        acc[2] += in0 ? (double)sd : 0.0;
+                        acc[3] += in1 ? (double)sd : 0.0;
+                        acc[4] += in2 ? (double)sd : 0.0;
+                    } else {
+#pragma unroll
+                        for (int rr = 0; rr < YA; ++rr) {
+                            const int y = r + (i + YB * rr) * g.P;
+                            const C2 u = v[c][rr];
+                            const double d = (double)u.x * (double)u.x + (double)u.y * (double)u.y;
+                            double V = 0.0;
+                            if (a.vform_obs == VF_DENSE) V = (double)k.Vd[pbase + ((long long)y << g.lgnx) + x];
+                            else if (a.vform_obs == VF_PRODUCT) V = a.rd.g64[y] * hz + vz64;
+                            else if (a.vform_obs == VF_SEPARABLE) V = vxz + a.rd.Vsep[g.nx + y];
+                            acc[0] += d;
+                            acc[1] += V * d;
+                            acc[2] += in0 ? d : 0.0;
+                            acc[3] += in1 ? d : 0.0;
+                            acc[4] += in2 ? d : 0.0;
+                        }
                     }
                 }
                 if (!HOT && (flags & XY_GRAD_PRE)) grad_task(v[c], i, x);
@@ -450,6 +489,8 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                     for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], fmadd(gtab[i + YB * rr], hx, thz), 1);
                     // (the hot variant is only chosen when the short series applies)
                 } else if (kick) {
+                    // norm partial of the column in the element type (FP32 for complex64)
+                    T nrm = T(0);
                     if (k.form == VF_SEPARABLE) {
                         const Lift<T> *tb = full ? k.sep_full : k.sep_half;
                         const Lift<T> lx = tb[x], lz = tb[g.nx + g.ny + zl];
@@ -458,8 +499,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                         for (int rr = 0; rr < YA; ++rr) {
                             const int jy = i + YB * rr;
                             kick_sep<T>(v[c][rr], lx, ytab[jy], lz, k.imag);
-                            if (flags & XY_RED_NORM)
-                                acc[0] += (double)v[c][rr].x * (double)v[c][rr].x + (double)v[c][rr].y * (double)v[c][rr].y;
+                            if (flags & XY_RED_NORM) nrm += norm2(v[c][rr]);
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
                         }
@@ -481,8 +521,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                                     ? fmadd(gtab[jy], hx, thz)
                                     : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
                             kick_one<T>(v[c][rr], th, k.imag, small);
-                            if (flags & XY_RED_NORM)
-                                acc[0] += (double)v[c][rr].x * (double)v[c][rr].x + (double)v[c][rr].y * (double)v[c][rr].y;
+                            if (flags & XY_RED_NORM) nrm += norm2(v[c][rr]);
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
                         }
@@ -498,6 +537,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                             }
                         }
                     }
+                    if (flags & XY_RED_NORM) acc[0] += (double)nrm;
                 }
             }
             if constexpr (OUT_MIXED) {
@@ -648,6 +688,8 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
     for (int e = t; e < NZ; e += NT) {
         wz[e] = a.tw[g.fast_z_off + e];
         if (!a.observe) kz[e] = a.kin[g.nx + g.ny + e];
+        else if constexpr (std::is_same<T, float>::value)        // k_z^2/2 in FP32
+            reinterpret_cast<float *>(kz)[e] = (float)a.k2h[g.nx + g.ny + e];
     }
 
     Lift<T> cw[P];
@@ -739,12 +781,24 @@ __global__ void __launch_bounds__(z_threads<T>(NZ), (sizeof(T) == 4 && P * W == 
             // register brev(k2) holds kz = jp + ZA k2
             if (a.observe) {
                 const double kxy = a.k2h[kx] + a.k2h[g.nx + ky];
-                sfor<ZB>([&](auto kc) {
-                    constexpr int k2 = decltype(kc)::value;
-                    const C2 u = v[brev(k2, ZB)];
-                    acc[0] += (kxy + a.k2h[g.nx + g.ny + jp + ZA * k2]) *
-                              ((double)u.x * (double)u.x + (double)u.y * (double)u.y);
-                });
+                if constexpr (std::is_same<T, float>::value) {
+                    // complex64: the task's 32 terms in FP32, FP64 from there on
+                    const float *k2z = reinterpret_cast<const float *>(kz);
+                    const float kxyf = (float)kxy;
+                    float sk = 0.0f;
+                    sfor<ZB>([&](auto kc) {
+                        constexpr int k2 = decltype(kc)::value;
+                        sk = fmadd(kxyf + k2z[jp + ZA * k2], norm2(v[brev(k2, ZB)]), sk);
+                    });
+                    acc[0] += sk;
+                } else {
+                    sfor<ZB>([&](auto kc) {
+                        constexpr int k2 = decltype(kc)::value;
+                        const C2 u = v[brev(k2, ZB)];
+                        acc[0] += (kxy + a.k2h[g.nx + g.ny + jp + ZA * k2]) *
+                                  ((double)u.x * (double)u.x + (double)u.y * (double)u.y);
+                    });
+                }
                 continue;
             }
             const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky];
