@@ -70,6 +70,27 @@ def dist_info():
     return rank, world, local
 
 
+def combine_ranks(ms, e2e_value, steps, world, reduce):
+    """Whole-job numbers of a replica run: the step time is the slowest
+    rank's, `value` counts the split steps of all ranks, the e2e rate is the
+    slowest rank's times the number of ranks.  reduce(x, "max"|"min") combines
+    a float over ranks (identity for one rank)."""
+    ms_max = reduce(ms, "max")
+    e2e_total = reduce(e2e_value, "min") * world
+    value = steps * SPLIT * world / (ms_max / 1000.0)
+    return ms_max, value, e2e_total
+
+
+def make_reduce(dist, torch, device):
+    def reduce(x, op):
+        if dist is None:
+            return float(x)
+        t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.MIN)
+        return float(t.item())
+    return reduce
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -174,7 +195,10 @@ def initial_state(wl, dtype_t, torch, device):
     return torch.from_numpy(psi).to(device=device, dtype=dtype_t)
 
 
-def time_path(ctap, wl, torch, dtype, split, steps, warmup, device, stream, profile=True):
+def time_path(ctap, wl, torch, dtype, split, steps, warmup, device, stream, profile=True,
+              barrier=None):
+    """W untimed warm-up bench steps, then exactly K timed ones, bracketed by
+    barrier() (all ranks) and a device synchronisation on both sides."""
     plan = build_plan(ctap, wl, dtype, stream)
     t = torch.complex64 if dtype == "c64" else torch.complex128
     psi = initial_state(wl, t, torch, device)
@@ -183,6 +207,8 @@ def time_path(ctap, wl, torch, dtype, split, steps, warmup, device, stream, prof
             plan.step(psi, split, DT)
             plan.observables(psi)
     torch.cuda.synchronize()
+    if barrier is not None:
+        barrier()
     plan.set_profiling(profile)
     plan.pass_times()
     launches0 = plan.launch_count
@@ -197,6 +223,8 @@ def time_path(ctap, wl, torch, dtype, split, steps, warmup, device, stream, prof
             obs = plan.observables(psi)
         e1.record(stream)
         torch.cuda.synchronize()
+    if barrier is not None:
+        barrier()
     ms = e0.elapsed_time(e1)
     launches = plan.launch_count - launches0
     counts, pms = plan.pass_times()
@@ -496,21 +524,15 @@ def run_ours(a):
     build.build()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
     stream = torch.cuda.Stream(device=device)
+    reduce = make_reduce(dist, torch, device)
 
-    if world > 1:
-        dist.barrier()
-    res = time_path(ctap, wl, torch, "c64", SPLIT, a.steps, a.warmup, device, stream)
-    ms = res["ms"]
-    if world > 1:
-        tt = torch.tensor([ms], device=device, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    split_total = a.steps * SPLIT * world
-    value = split_total / (ms / 1000.0)
+    res = time_path(ctap, wl, torch, "c64", SPLIT, a.steps, a.warmup, device, stream,
+                    barrier=dist.barrier if dist is not None else None)
 
     N = int(np.prod(SHAPE))
     esize = 8
@@ -550,7 +572,7 @@ def run_ours(a):
                                    + "_kernel<double>",
                          "flops_per_point": fxy if k64 == 0 else fz},
             "hbm_frac_of_dominant_kernel": ach64 / hbm,
-            "fp32_speedup": (1000.0 / (ms / (a.steps * SPLIT))) / (1000.0 / ms64),
+            "fp32_speedup": (1000.0 / (res["ms"] / (a.steps * SPLIT))) / (1000.0 / ms64),
             "dtype": "f64", "obs": [float(x) for x in r64["obs"]]}
         del r64
         rdf = time_path(ctap, wl, torch, "c128df", SPLIT_FP64, max(2, a.steps // 10), 1, device,
@@ -569,10 +591,7 @@ def run_ours(a):
         extra["cufft_comparison"] = time_cufft(torch, device, stream, res["plan"])
         extra["cpu_baseline"] = cpu_baseline()
     e2e = time_e2e(ctap, wl, torch, max(3, a.steps // 4), device, stream, res["plan"])
-    if world > 1:
-        tt = torch.tensor([e2e["value"]], device=device, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MIN)
-        e2e["value"] = float(tt.item()) * world
+    ms, value, e2e["value"] = combine_ranks(res["ms"], e2e["value"], a.steps, world, reduce)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
