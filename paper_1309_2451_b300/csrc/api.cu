@@ -234,7 +234,11 @@ template <class T> XYArgs<T> xy_args(PlanState &st, const TabSet *ts, double dt,
     a.vform_obs = st.vform;
     a.partials = st.d_partials;
     // short kick series: |V| dt <= 0.5 (FP32 series) or <= 0.1 (FP64 series)
-    a.small_angle = (st.vmax * std::fabs(dt) <= (sizeof(T) == 4 ? 0.5 : 0.1)) ? 1 : 0;
+    // short kick series: |V| dt <= 0.5 (FP32 series) or <= 0.1 (FP64 series);
+    // complex64 also has a shorter series for |V| dt <= 0.16
+    const double vdt = st.vmax * std::fabs(dt);
+    a.small_angle = (vdt <= (sizeof(T) == 4 ? 0.5 : 0.1)) ? 1 : 0;
+    if (std::is_same<T, float>::value && vdt <= 0.16) a.small_angle = 2;
     return a;
 }
 

@@ -64,9 +64,24 @@ __device__ __forceinline__ void lift_small(float th, float &p, float &u)
 
 // exp(-i th) for the real-time kick: the short series for complex64 when
 // |th| <= 0.5, the general half-turn reduction otherwise (always for FP64)
+// |th| <= 0.16: the same odd series truncated after the fifth-order terms
+// (omitted terms below th^7/5040 = 5e-10 and 17 (th/2)^7/315 = 1e-9)
+__device__ __forceinline__ void lift_tiny(float th, float &p, float &u)
+{
+    const float a = -th, a2 = a * a;
+    u = fmadd(a2 * a, fmadd(a2, 8.33333333e-03f, -1.66666667e-01f), a);     // a - a^3/6 + a^5/120
+    const float h = 0.5f * a, h2 = h * h;
+    p = -fmadd(h2 * h, fmadd(h2, 1.33333333e-01f, 3.33333333e-01f), h);    // -(h + h^3/3 + 2h^5/15)
+}
+
+// small: 2 for |th| <= 0.16, 1 for |th| <= 0.5, 0 for any angle
 __device__ __forceinline__ void kick_rt(float2 &v, float th, int small)
 {
-    if (small) {
+    if (small == 2) {
+        float p, u;
+        lift_tiny(th, p, u);
+        rot_f<float>(v, p, u);
+    } else if (small) {
         float p, u;
         lift_small(th, p, u);
         rot_f<float>(v, p, u);
@@ -485,8 +500,9 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                 if (!HOT && (flags & XY_GRAD_PRE)) grad_task(v[c], i, x);
                 if (HOT) {
                     const T hx = htab[p];
+                    const int tier = a.small_angle;     // 1 or 2 (uniform across the grid)
 #pragma unroll
-                    for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], fmadd(gtab[i + YB * rr], hx, thz), 1);
+                    for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], fmadd(gtab[i + YB * rr], hx, thz), tier);
                     // (the hot variant is only chosen when the short series applies)
                 } else if (kick) {
                     // norm partial of the column in the element type (FP32 for complex64)

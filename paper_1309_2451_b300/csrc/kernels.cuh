@@ -106,7 +106,7 @@ template <class T> struct XYArgs {
     Cx<T> *state_out;         // XY_STATE_OUT target (natural layout) or null
     double *partials;         // per-CTA reduction results
     int flags;
-    int small_angle;          // |V| dt <= 0.5 everywhere: no half-turn reduction
+    int small_angle;          // kick series tier: 0 any angle, 1 |V| dt <= 0.5, 2 (complex64) <= 0.16
     GradData gd;
 };
 
