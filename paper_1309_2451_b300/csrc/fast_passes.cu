@@ -1133,37 +1133,45 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
         }
         __syncthreads();
 
-        // Z5: inverse cross DFT and store, one chunk (128 z-rows) per round;
-        // as soon as chunk m < NCH/2 is drained, chunk NCH/2 + m of the next
-        // tile is copied into its slot
+        // Z5: the whole tile is read back to registers first (8 rounds of
+        // 4 x 16 bytes per thread; the cross twiddles too), so every ring
+        // slot is free before the stores start: the next tile's second half
+        // is copied in while this tile's inverse cross DFTs and stores run,
+        // and no store waits for registers a later load would overwrite
+        C2 v[NCH][2][P];
+#pragma unroll
         for (int m = 0; m < NCH; ++m) {
             const int q = m * CHZ * (W / 2) + t;
             const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
-            C2 v[2][P];
             sfor<P>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
                 const float4 w4 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + xo));
-                v[0][brev(k2, P)] = make_float2(w4.x, w4.y);
-                v[1][brev(k2, P)] = make_float2(w4.z, w4.w);
+                v[m][0][brev(k2, P)] = make_float2(w4.x, w4.y);
+                v[m][1][brev(k2, P)] = make_float2(w4.z, w4.w);
             });
+        }
+        Lift<T> cw[P];
+#pragma unroll
+        for (int rr = 1; rr < P; ++rr) cw[rr] = tb[W + P + rr];
+        __syncthreads();                         // tile i's chunks and tables are free
+        if (i + 1 < nmine) issue(i + 1, NCH / 2, NCH);
+        cp_async_commit();
+#pragma unroll
+        for (int m = 0; m < NCH; ++m) {
+            const int q = m * CHZ * (W / 2) + t;
+            const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                dft_inv<P, 0, 1, T>(v[c]);
+                dft_inv<P, 0, 1, T>(v[m][c]);
 #pragma unroll
-                for (int rr = 1; rr < P; ++rr) lift_b<T>(v[c][rr], tb[W + P + rr]);
+                for (int rr = 1; rr < P; ++rr) lift_b<T>(v[m][c][rr], cw[rr]);
             }
             C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
 #pragma unroll
             for (int rr = 0; rr < P; ++rr)
                 __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
-                       make_float4(v[0][rr].x, v[0][rr].y, v[1][rr].x, v[1][rr].y));
-            if (m < NCH / 2) {
-                __syncthreads();                 // chunk m drained by every thread
-                if (i + 1 < nmine) issue(i + 1, NCH / 2 + m, NCH / 2 + m + 1);
-                cp_async_commit();
-            }
+                       make_float4(v[m][0][rr].x, v[m][0][rr].y, v[m][1][rr].x, v[m][1][rr].y));
         }
-        __syncthreads();                         // tile i's chunks are free
     }
     cp_async_wait<0>();
 }
