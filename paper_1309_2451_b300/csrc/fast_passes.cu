@@ -34,6 +34,7 @@
 //   the z-major accesses of Z1/Z5 and the column accesses of Z2-Z4 are both
 //   free of bank conflicts.
 #include <algorithm>
+#include <cstdint>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -912,7 +913,17 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// one 32-byte row segment (four complex64 values) in one 256-bit streaming
+// store; the address must be 32-byte aligned
+__device__ __forceinline__ void st_stream_seg(float2 *p, float2 a, float2 b, float2 c, float2 d)
+{
+    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "f"(a.x),
+                 "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
+                 : "memory");
+}
+
 constexpr int kRingCHZ = 128;            // z-rows per ring chunk
+constexpr int kRingNT = 256;             // threads of a ring CTA
 
 }  // namespace
 
@@ -922,8 +933,10 @@ constexpr int kRingCHZ = 128;            // z-rows per ring chunk
 // blockIdx.x, blockIdx.x + gridDim.x, ...  The tile lives in a ring of
 // twelve 128-row chunks of shared memory (a tile is eight chunks).  While a
 // tile is transformed, 16-byte asynchronous copies (cp.async, no registers
-// held) bring in the first half of the next tile; its second half follows as
-// soon as the store phase has drained the current tile's first half.  The
+// held) bring in the first half of the next tile, one chunk after each of
+// the four transform phases so that the copy requests trickle out between
+// arithmetic instead of stalling every warp at once; the second half follows
+// as soon as the store phase has read the current tile back.  The
 // HBM load latency of a tile is thereby hidden behind the previous tile's
 // shared-memory phases instead of stalling the SM.
 //
@@ -931,14 +944,15 @@ constexpr int kRingCHZ = 128;            // z-rows per ring chunk
 // z_fast_kernel, Z5 inverse cross DFT and streaming stores.  Same arithmetic
 // and HBM layout as z_fast_kernel.
 
-template <int NZ, int ZA, int ZB, int P, int W>
-__global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, int ntiles)
+template <int NZ, int ZA, int ZB, int P, int W, int NT>
+__global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int ntiles)
 {
     static_assert(ZA * ZB == NZ && ZA == 32 && ZB == 32, "1024-point lines as 32 x 32");
     static_assert(P * W == 16 && W == 4, "16-column tiles of 32-byte row segments");
+    static_assert((NT == 256 || NT == 512) && kRingCHZ % (NT / 8) == 0 && NZ % NT == 0,
+                  "copy and read-back rounds divide evenly");
     using T = float;
     using C2 = float2;
-    constexpr int NT = 256;
     constexpr int C = P * W;
     constexpr int CHZ = kRingCHZ;
     constexpr int NCH = NZ / CHZ;                  // chunks per tile (8)
@@ -1017,12 +1031,8 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
         const int tl = tile & ((1 << g.lgzt) - 1);
         const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
         const long long roff = (long long)(tile >> g.lgzt) * g.rstride;
-        if (i + 1 < nmine) {
-            issue(i + 1, 0, NCH / 2);
-            load_tabs(i + 1);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
+        if (i + 1 < nmine) load_tabs(i + 1);
+        cp_async_wait<0>();
         __syncthreads();                         // tile i (and its tables) visible
         const Lift<T> *tb = tabs[i & 1];
 
@@ -1057,6 +1067,7 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
                 *reinterpret_cast<float4 *>(ring + at(zz, k2 * W + xo)) = make_float4(e0.x, e0.y, e1.x, e1.y);
             });
         }
+        if (i + 1 < nmine) issue(i + 1, 0, 1);   // next tile, first half, chunk 0
         __syncthreads();
 
         // Z2: forward z, first stage (radix ZA) on rows j + ZB rr, in place.
@@ -1073,6 +1084,7 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
                 ring[sb[kk / 4] + (kk % 4) * ZB * C + off] = v[brev(kk, ZA)];
             });
         }
+        if (i + 1 < nmine) issue(i + 1, 1, 2);   // next tile, first half, chunk 1
         __syncthreads();
 
         // Z3: last stage on the contiguous rows ZB jp + j, kinetic factor, inverse
@@ -1116,6 +1128,7 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
 #pragma unroll
             for (int j = 0; j < ZB; ++j) ring[rowbase + j * C + (col ^ ((j & SWM) * W))] = v[j];
         }
+        if (i + 1 < nmine) issue(i + 1, 2, 3);   // next tile, first half, chunk 2
         __syncthreads();
 
         // Z4: inverse z, first stage, in place
@@ -1131,23 +1144,30 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
 #pragma unroll
             for (int rr = 0; rr < ZA; ++rr) ring[sb[rr / 4] + (rr % 4) * ZB * C + off] = v[rr];
         }
+        if (i + 1 < nmine) issue(i + 1, 3, 4);   // next tile, first half, chunk 3
+        cp_async_commit();
         __syncthreads();
 
-        // Z5: the whole tile is read back to registers first (8 rounds of
-        // 4 x 16 bytes per thread; the cross twiddles too), so every ring
+        // Z5: the whole tile is read back to registers first (R5 z-rows of
+        // 4 x 32 bytes per thread; the cross twiddles too), so every ring
         // slot is free before the stores start: the next tile's second half
         // is copied in while this tile's inverse cross DFTs and stores run,
-        // and no store waits for registers a later load would overwrite
-        C2 v[NCH][2][P];
+        // and no store waits for registers a later load would overwrite.
+        // A thread owns whole 32-byte row segments (the W columns of one
+        // row), written with one 256-bit store each.
+        constexpr int R5 = NZ / NT;
+        C2 v[R5][W][P];
 #pragma unroll
-        for (int m = 0; m < NCH; ++m) {
-            const int q = m * CHZ * (W / 2) + t;
-            const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
+        for (int m = 0; m < R5; ++m) {
+            const int zz = m * NT + t;
             sfor<P>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                const float4 w4 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + xo));
-                v[m][0][brev(k2, P)] = make_float2(w4.x, w4.y);
-                v[m][1][brev(k2, P)] = make_float2(w4.z, w4.w);
+                const float4 *seg = reinterpret_cast<const float4 *>(ring + at(zz, k2 * W));
+                const float4 w0 = seg[0], w1 = seg[1];
+                v[m][0][brev(k2, P)] = make_float2(w0.x, w0.y);
+                v[m][1][brev(k2, P)] = make_float2(w0.z, w0.w);
+                v[m][2][brev(k2, P)] = make_float2(w1.x, w1.y);
+                v[m][3][brev(k2, P)] = make_float2(w1.z, w1.w);
             });
         }
         Lift<T> cw[P];
@@ -1157,20 +1177,18 @@ __global__ void __launch_bounds__(256, 1) z_ring_kernel(const ZArgs<float> a, in
         if (i + 1 < nmine) issue(i + 1, NCH / 2, NCH);
         cp_async_commit();
 #pragma unroll
-        for (int m = 0; m < NCH; ++m) {
-            const int q = m * CHZ * (W / 2) + t;
-            const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
+        for (int m = 0; m < R5; ++m) {
+            const int zz = m * NT + t;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < W; ++c) {
                 dft_inv<P, 0, 1, T>(v[m][c]);
 #pragma unroll
                 for (int rr = 1; rr < P; ++rr) lift_b<T>(v[m][c][rr], cw[rr]);
             }
-            C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
+            float2 *p = a.dst + (long long)zz * g.plane + colbase;
 #pragma unroll
             for (int rr = 0; rr < P; ++rr)
-                __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
-                       make_float4(v[m][0][rr].x, v[m][0][rr].y, v[m][1][rr].x, v[m][1][rr].y));
+                st_stream_seg(p + ((long long)rr << g.lgnx), v[m][0][rr], v[m][1][rr], v[m][2][rr], v[m][3][rr]);
         }
     }
     cp_async_wait<0>();
@@ -1235,19 +1253,20 @@ bool try_z(const ZArgs<T> &a, cudaStream_t st)
         cfg = true;
     }
     if constexpr (std::is_same<T, float>::value && NZ == 1024 && P == 4 && W == 4) {
-        if (a.ring && !a.observe && a.src == a.dst) {
+        // the ring's 256-bit stores need a 32-byte aligned psi
+        if (a.ring && !a.observe && a.src == a.dst && (reinterpret_cast<uintptr_t>(a.dst) & 31) == 0) {
             constexpr int NRING = 12;
             const size_t rsmem = (size_t)NRING * kRingCHZ * P * W * sizeof(Cx<T>) +
                                  2 * NZ * sizeof(Lift<T>);
             static bool rcfg = false;
             if (!rcfg) {
-                cudaFuncSetAttribute(z_ring_kernel<NZ, ZA, ZB, P, W>,
+                cudaFuncSetAttribute(z_ring_kernel<NZ, ZA, ZB, P, W, kRingNT>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
                 rcfg = true;
             }
             const int ntiles = z_grid(a.g);
             const int grid = std::min(ntiles, sm_count());
-            z_ring_kernel<NZ, ZA, ZB, P, W><<<grid, 256, rsmem, st>>>(a, ntiles);
+            z_ring_kernel<NZ, ZA, ZB, P, W, kRingNT><<<grid, kRingNT, rsmem, st>>>(a, ntiles);
             return true;
         }
     }

@@ -381,6 +381,27 @@ def test_persistent_z_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
     assert rel(ring, ref) < 1e-6
 
 
+def test_ring_with_16_byte_aligned_psi(ctap):
+    """The persistent Z pass stores 32-byte row segments with 256-bit stores;
+    a psi view that is 16- but not 32-byte aligned takes the one-tile-per-CTA
+    Z pass instead, with the same result."""
+    shape, box = (1024, 256, 64), wl.CTAP_BOX
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=16)
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    psi = to_dev(psi0, "c64")
+    plan.step(psi, 2, 0.0025)
+    aligned = psi.cpu().numpy().astype(complex)
+    n = int(np.prod(shape))
+    buf = torch.zeros(n + 2, dtype=torch.complex64, device="cuda")
+    view = buf[2:].view(shape)
+    assert view.data_ptr() % 32 == 16
+    view.copy_(to_dev(psi0, "c64"))
+    plan.step(view, 2, 0.0025)
+    assert rel(view.cpu().numpy().astype(complex), aligned) < 1e-6
+    ref = oracle.step(psi0, V, box, 0.0025, 2)
+    assert rel(aligned, ref) < 1e-6
+
+
 FAST128_SHAPES = [(256, 128, 128), (256, 256, 256), (512, 256, 256), (1024, 128, 256),
                   (64, 64, 64), (16, 32, 128)]
 
