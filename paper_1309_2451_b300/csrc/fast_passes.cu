@@ -959,6 +959,11 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
     constexpr int NRING = NCH + NCH / 2;           // ring slots (12)
     constexpr int CHE = CHZ * C;                   // complex values per chunk
     constexpr int SWM = 16 / W - 1;
+    // shared-memory swizzle of a 16-column z-row: the 32-byte group of each
+    // row class moves with z mod 4 and its 16-byte halves swap with bit 2 of
+    // z, so that every access pattern below (16-byte copies and reads of
+    // eight z-rows, 8-byte column sweeps) meets each bank once per wavefront
+    auto swz = [](int z) { return ((z & SWM) * W) | (((z >> 2) & 1) * 2); };
     extern __shared__ __align__(16) unsigned char smraw[];
     C2 *ring = reinterpret_cast<C2 *>(smraw);
     Lift<T> *wz = reinterpret_cast<Lift<T> *>(ring + NRING * CHE);
@@ -981,7 +986,7 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
     // Thread t always moves the same 16-byte piece (half h of row class r)
     // of z-rows t/8 + 32 m, so its addresses advance by fixed strides.
     const int ch = t & 1, cr = (t >> 1) & (P - 1), czl = t >> 3;
-    const int cdst = czl * C + ((cr * W + 2 * ch) ^ ((czl & SWM) * W));
+    const int cdst = czl * C + ((cr * W + 2 * ch) ^ swz(czl));
     auto issue = [&](int i, int c0, int c1) {
         const int tile = blockIdx.x + i * G;
         const int tl = tile & ((1 << g.lgzt) - 1);
@@ -1041,7 +1046,7 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
         for (int c = 0; c < NCH; ++c) sb[c] = slot_of(i, c) * CHE;
         auto at = [&](int zz, int col) {
             int s = slot_of(i, zz / CHZ);
-            return s * CHE + (zz % CHZ) * C + (col ^ ((zz & SWM) * W));
+            return s * CHE + (zz % CHZ) * C + (col ^ swz(zz));
         };
         const long long colbase = roff + ((long long)(kp * P) << g.lgnx) + (b * W);
 
@@ -1074,7 +1079,7 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
         // Row j + ZB rr lies in chunk rr / 4 (ZB = 32, 128-row chunks).
         for (int q = t; q < C * ZB; q += NT) {
             const int col = q % C, j = q / C;
-            const int off = j * C + (col ^ ((j & SWM) * W));
+            const int off = j * C + (col ^ swz(j));
             C2 v[ZA];
 #pragma unroll
             for (int rr = 0; rr < ZA; ++rr) v[rr] = ring[sb[rr / 4] + (rr % 4) * ZB * C + off];
@@ -1093,7 +1098,7 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
             const int rowbase = slot_of(i, (ZB * jp) / CHZ) * CHE + ((ZB * jp) % CHZ) * C;
             C2 v[ZB];
 #pragma unroll
-            for (int j = 0; j < ZB; ++j) v[j] = ring[rowbase + j * C + (col ^ ((j & SWM) * W))];
+            for (int j = 0; j < ZB; ++j) v[j] = ring[rowbase + j * C + (col ^ swz(j))];
             sfor<ZB - 1>([&](auto jc) {
                 constexpr int j = decltype(jc)::value + 1;
                 if constexpr (j % 4 == 0) hoist_fence();
@@ -1126,7 +1131,7 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
                 lift_b<T>(v[j], wz[jp * j]);
             });
 #pragma unroll
-            for (int j = 0; j < ZB; ++j) ring[rowbase + j * C + (col ^ ((j & SWM) * W))] = v[j];
+            for (int j = 0; j < ZB; ++j) ring[rowbase + j * C + (col ^ swz(j))] = v[j];
         }
         if (i + 1 < nmine) issue(i + 1, 2, 3);   // next tile, first half, chunk 2
         __syncthreads();
@@ -1134,7 +1139,7 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
         // Z4: inverse z, first stage, in place
         for (int q = t; q < C * ZB; q += NT) {
             const int col = q % C, j = q / C;
-            const int off = j * C + (col ^ ((j & SWM) * W));
+            const int off = j * C + (col ^ swz(j));
             C2 v[ZA];
             sfor<ZA>([&](auto kc) {
                 constexpr int kk = decltype(kc)::value;
@@ -1162,8 +1167,8 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
             const int zz = m * NT + t;
             sfor<P>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                const float4 *seg = reinterpret_cast<const float4 *>(ring + at(zz, k2 * W));
-                const float4 w0 = seg[0], w1 = seg[1];
+                const float4 w0 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W));
+                const float4 w1 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + 2));
                 v[m][0][brev(k2, P)] = make_float2(w0.x, w0.y);
                 v[m][1][brev(k2, P)] = make_float2(w0.z, w0.w);
                 v[m][2][brev(k2, P)] = make_float2(w1.x, w1.y);
