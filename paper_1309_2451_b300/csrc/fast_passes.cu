@@ -34,7 +34,6 @@
 //   the z-major accesses of Z1/Z5 and the column accesses of Z2-Z4 are both
 //   free of bank conflicts.
 #include <algorithm>
-#include <cstdint>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -913,15 +912,6 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// one 32-byte row segment (four complex64 values) in one 256-bit streaming
-// store; the address must be 32-byte aligned
-__device__ __forceinline__ void st_stream_seg(float2 *p, float2 a, float2 b, float2 c, float2 d)
-{
-    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "f"(a.x),
-                 "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
-                 : "memory");
-}
-
 constexpr int kRingCHZ = 128;            // z-rows per ring chunk
 constexpr int kRingNT = 256;             // threads of a ring CTA
 
@@ -949,7 +939,7 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
 {
     static_assert(ZA * ZB == NZ && ZA == 32 && ZB == 32, "1024-point lines as 32 x 32");
     static_assert(P * W == 16 && W == 4, "16-column tiles of 32-byte row segments");
-    static_assert((NT == 256 || NT == 512) && kRingCHZ % (NT / 8) == 0 && NZ % NT == 0,
+    static_assert((NT == 256 || NT == 512) && kRingCHZ % (NT / 8) == 0 && NZ * (W / 2) % NT == 0,
                   "copy and read-back rounds divide evenly");
     using T = float;
     using C2 = float2;
@@ -1153,26 +1143,25 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
         cp_async_commit();
         __syncthreads();
 
-        // Z5: the whole tile is read back to registers first (R5 z-rows of
-        // 4 x 32 bytes per thread; the cross twiddles too), so every ring
+        // Z5: the whole tile is read back to registers first (R5 rounds of
+        // 4 x 16 bytes per thread; the cross twiddles too), so every ring
         // slot is free before the stores start: the next tile's second half
         // is copied in while this tile's inverse cross DFTs and stores run,
         // and no store waits for registers a later load would overwrite.
-        // A thread owns whole 32-byte row segments (the W columns of one
-        // row), written with one 256-bit store each.
-        constexpr int R5 = NZ / NT;
-        C2 v[R5][W][P];
+        // Two lanes write the two halves of each 32-byte row segment in the
+        // same instruction (16 sectors per warp store: measured to drain
+        // faster per SM than one lane per segment with 256-bit stores).
+        constexpr int R5 = NZ * (W / 2) / NT;
+        C2 v[R5][2][P];
 #pragma unroll
         for (int m = 0; m < R5; ++m) {
-            const int zz = m * NT + t;
+            const int q = m * NT + t;
+            const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
             sfor<P>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                const float4 w0 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W));
-                const float4 w1 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + 2));
-                v[m][0][brev(k2, P)] = make_float2(w0.x, w0.y);
-                v[m][1][brev(k2, P)] = make_float2(w0.z, w0.w);
-                v[m][2][brev(k2, P)] = make_float2(w1.x, w1.y);
-                v[m][3][brev(k2, P)] = make_float2(w1.z, w1.w);
+                const float4 w4 = *reinterpret_cast<const float4 *>(ring + at(zz, k2 * W + xo));
+                v[m][0][brev(k2, P)] = make_float2(w4.x, w4.y);
+                v[m][1][brev(k2, P)] = make_float2(w4.z, w4.w);
             });
         }
         Lift<T> cw[P];
@@ -1183,17 +1172,19 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
         cp_async_commit();
 #pragma unroll
         for (int m = 0; m < R5; ++m) {
-            const int zz = m * NT + t;
+            const int q = m * NT + t;
+            const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
 #pragma unroll
-            for (int c = 0; c < W; ++c) {
+            for (int c = 0; c < 2; ++c) {
                 dft_inv<P, 0, 1, T>(v[m][c]);
 #pragma unroll
                 for (int rr = 1; rr < P; ++rr) lift_b<T>(v[m][c][rr], cw[rr]);
             }
-            float2 *p = a.dst + (long long)zz * g.plane + colbase;
+            C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
 #pragma unroll
             for (int rr = 0; rr < P; ++rr)
-                st_stream_seg(p + ((long long)rr << g.lgnx), v[m][0][rr], v[m][1][rr], v[m][2][rr], v[m][3][rr]);
+                __stcs(reinterpret_cast<float4 *>(p + ((long long)rr << g.lgnx)),
+                       make_float4(v[m][0][rr].x, v[m][0][rr].y, v[m][1][rr].x, v[m][1][rr].y));
         }
     }
     cp_async_wait<0>();
@@ -1258,8 +1249,7 @@ bool try_z(const ZArgs<T> &a, cudaStream_t st)
         cfg = true;
     }
     if constexpr (std::is_same<T, float>::value && NZ == 1024 && P == 4 && W == 4) {
-        // the ring's 256-bit stores need a 32-byte aligned psi
-        if (a.ring && !a.observe && a.src == a.dst && (reinterpret_cast<uintptr_t>(a.dst) & 31) == 0) {
+        if (a.ring && !a.observe && a.src == a.dst) {
             constexpr int NRING = 12;
             const size_t rsmem = (size_t)NRING * kRingCHZ * P * W * sizeof(Cx<T>) +
                                  2 * NZ * sizeof(Lift<T>);

@@ -382,9 +382,9 @@ def test_persistent_z_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
 
 
 def test_ring_with_16_byte_aligned_psi(ctap):
-    """The persistent Z pass stores 32-byte row segments with 256-bit stores;
-    a psi view that is 16- but not 32-byte aligned takes the one-tile-per-CTA
-    Z pass instead, with the same result."""
+    """The persistent Z pass moves 16-byte pieces: a psi view that is 16- but
+    not 32-byte aligned (row segments then straddle 32-byte sectors) gives
+    the same result as an aligned one."""
     shape, box = (1024, 256, 64), wl.CTAP_BOX
     psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=16)
     plan, V, c = guides_plan(ctap, shape, box, "c64")
