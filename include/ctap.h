@@ -229,6 +229,7 @@ ctap_status ctap_pass_times(ctap_plan_t plan, long long counts[3], double ms[3])
  * info[1] = rows per XY tile, info[2] = columns per Z tile, info[3] = bytes
  * of one psi, info[4] = fast-pass mask (1: specialised XY pass, 2:
  * specialised Z pass, 4: the in-place Z pass runs as the persistent ring
+ * kernel, 8: the steady in-place XY pass runs as the persistent ring
  * kernel). */
 ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);
 

@@ -233,12 +233,12 @@ template <class T> XYArgs<T> xy_args(PlanState &st, const TabSet *ts, double dt,
     a.rd.k2h = st.d_k2h;
     a.vform_obs = st.vform;
     a.partials = st.d_partials;
-    // short kick series: |V| dt <= 0.5 (FP32 series) or <= 0.1 (FP64 series)
     // short kick series: |V| dt <= 0.5 (FP32 series) or <= 0.1 (FP64 series);
     // complex64 also has a shorter series for |V| dt <= 0.16
     const double vdt = st.vmax * std::fabs(dt);
     a.small_angle = (vdt <= (sizeof(T) == 4 ? 0.5 : 0.1)) ? 1 : 0;
     if (std::is_same<T, float>::value && vdt <= 0.16) a.small_angle = 2;
+    a.ring = st.no_ring ? 0 : 1;
     return a;
 }
 
@@ -1255,7 +1255,9 @@ ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5])
     info[3] = st->N * st->esize;
     const bool ring = st->fast_z && !st->no_ring && st->dtype == CTAP_C64 && st->nz == 1024 &&
                       st->geom.P == 4 && st->geom.w == 4;
-    info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0) | (ring ? 4 : 0);
+    const bool xy_ring = st->fast_xy && !st->no_ring && st->dtype == CTAP_C64 && st->nx == 256 &&
+                         st->geom.Ly == 64;
+    info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0) | (ring ? 4 : 0) | (xy_ring ? 8 : 0);
     return CTAP_OK;
 }
 

@@ -917,6 +917,240 @@ constexpr int kRingNT = 256;             // threads of a ring CTA
 
 }  // namespace
 
+// =================================================================== XY ring
+// Persistent form of the steady complex64 XY pass (nx = 256, 64-row tiles,
+// product potential, real time, in place): one 1024-thread CTA per SM walks
+// over the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  A tile is two
+// 32-row halves in a ring of three half buffers (3 x 32 x 258 x 8 B =
+// 198 KB).  The next tile's first half arrives by 16-byte asynchronous copies
+// (cp.async, no registers held), one 8-row round after each of the first
+// four transform phases, so that the copy requests leave between arithmetic;
+// its second half is issued as soon as the store phase has read the current
+// tile back into registers.  The last inverse x stage then reads shared
+// memory instead of HBM, and a tile's HBM load no longer stalls its SM.
+// Same arithmetic, tables and HBM layout as the steady xy_fast_kernel.
+template <int NX, int RA, int RB, int LY, int YA, int YB>
+__global__ void __launch_bounds__(1024, 1) xy_ring_kernel(const XYArgs<float> a, int ntiles)
+{
+    static_assert(RA * RB == NX && YA * YB == LY && LY == 64 && YA == 8 && YB == 8, "64-row tiles");
+    using T = float;
+    using C2 = float2;
+    constexpr int NT = 1024;
+    constexpr int PITCH = NX + 2;
+    constexpr int HR = LY / 2;                   // rows per half buffer
+    constexpr int HB = HR * PITCH;               // complex values per half buffer
+    constexpr int PPR = NX / 2;                  // 16-byte pieces per row
+    constexpr int RPI = NT / PPR;                // rows per copy round
+    constexpr int NCR = HR / RPI;                // copy rounds per half
+    static_assert(LY * RA == NT && LY * RB == NT && (NX / 2) * YA == NT && (NX / 2) * YB == NT &&
+                      NCR == 4 && HR % YA == 0,
+                  "one task per thread in every phase, four copy rounds per half");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2 *bufs = reinterpret_cast<C2 *>(smraw);
+    Lift<T> *wx = reinterpret_cast<Lift<T> *>(bufs + 3 * HB);   // as in xy_fast_kernel
+    Lift<T> *wy = wx + NX;
+    __shared__ T gtab[2][LY];                    // g(y) of the tile's rows, per tile
+    __shared__ T htab[2][NX];                    // H(x, z) tau at swapped position, per tile
+    __shared__ T thzs[2];                        // z-only phase, per tile
+
+    const Geom &g = a.g;
+    const Kick<T> &k = a.k;
+    const int t = threadIdx.x;
+    const int G = gridDim.x;
+    const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
+    const T tau = k.tau_full;
+    const int tier = a.small_angle;
+    auto unswx = [](int p) { return p / RA + RB * (p % RA); };
+    // half h of the i-th tile of this CTA: buffers rotate by two halves per tile
+    auto half_buf = [&](int i, int h) { return bufs + ((2 * i + h) % 3) * HB; };
+    const int cpiece = t % PPR, crow = t / PPR;
+    // copy rounds [m0, m1) of half h of the i-th tile: thread t moves piece
+    // t % PPR of rows crow + RPI m of the half
+    auto issue = [&](int i, int h, int m0, int m1) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        const C2 *src = a.src + (long long)z * g.plane +
+                        ((long long)((h * HR + crow + RPI * m0) * g.P + r) << g.lgnx) + 2 * cpiece;
+        C2 *dst = half_buf(i, h) + (crow + RPI * m0) * PITCH + 2 * cpiece;
+        const long long rstep = (long long)(RPI * g.P) << g.lgnx;
+        for (int m = m0; m < m1; ++m) {
+            cp_async16(dst, src);
+            src += rstep;
+            dst += RPI * PITCH;
+        }
+    };
+    auto load_tabs = [&](int i) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        if (t < LY) gtab[i & 1][t] = k.g[r + t * g.P];
+        if (t < NX) htab[i & 1][t] = k.H[(long long)z * g.nx + unswx(t)] * tau;
+        if (t == 0) thzs[i & 1] = k.vz ? k.vz[z & (g.nz - 1)] * tau : T(0);
+    };
+
+    if (nmine > 0) {
+        issue(0, 0, 0, NCR);
+        issue(0, 1, 0, NCR);
+        load_tabs(0);
+    }
+    cp_async_commit();
+    for (int e = t; e < NX + LY; e += NT)
+        wx[e] = e < NX ? a.tw[g.fast_x_off + (e % RA) * (e / RA)] : a.tw[g.fast_y_off + e - NX];
+
+    for (int i = 0; i < nmine; ++i) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        const bool more = i + 1 < nmine;
+        if (more) load_tabs(i + 1);
+        cp_async_wait<0>();
+        __syncthreads();                         // tile i (and its tables) visible
+        C2 *const b0 = half_buf(i, 0);
+        C2 *const b1 = half_buf(i, 1);
+        const T *gt = gtab[i & 1];
+        const T *ht = htab[i & 1];
+        const T thz = thzs[i & 1];
+
+        // P1: inverse x, last stage (radix RB) in place
+        {
+            const int j = t % RA, rw = t / RA;
+            C2 *rp = (rw < HR ? b0 : b1) + (rw % HR) * PITCH;
+            C2 v[RB];
+            sfor<RB>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                v[brev(kk, RB)] = rp[j + RA * kk];
+            });
+            dft_inv<RB, 0, 1, T>(v);
+#pragma unroll
+            for (int rr = 1; rr < RB; ++rr) lift_b<T>(v[rr], wx[rr * RA + j]);
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) rp[j + RA * rr] = v[rr];
+        }
+        if (more) issue(i + 1, 0, 0, 1);
+        __syncthreads();
+        // P2: inverse x, first stage (radix RA), in place on block j
+        {
+            const int rw = t % LY, j = t / LY;
+            C2 *bp = (rw < HR ? b0 : b1) + (rw % HR) * PITCH + RA * j;
+            C2 v[RA], w[RA];
+            load_pairs<RA>(bp, w);
+#pragma unroll
+            for (int kk = 0; kk < RA; ++kk) v[brev(kk, RA)] = w[kk];
+            dft_inv<RA, 0, 1, T>(v);
+            store_pairs<RA>(bp, v);
+        }
+        if (more) issue(i + 1, 0, 1, 2);
+        __syncthreads();
+        // P3a: inverse y, last stage (radix YB) on rows ii + YA kk, two
+        // columns; row ii + YA kk lies in the first half for kk < HR / YA
+        {
+            const int p = (t % (NX / 2)) * 2, ii = t / (NX / 2);
+            C2 *r0 = b0 + ii * PITCH + p, *r1 = b1 + ii * PITCH + p;
+            C2 v[YB], w[YB];
+            sfor<YB>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                ld2((kk < HR / YA ? r0 : r1) + YA * (kk % (HR / YA)) * PITCH, v[brev(kk, YB)],
+                    w[brev(kk, YB)]);
+            });
+            dft_inv<YB, 0, 1, T>(v);
+            dft_inv<YB, 0, 1, T>(w);
+#pragma unroll
+            for (int rr = 1; rr < YB; ++rr) {
+                const Lift<T> tw = wy[ii * rr];
+                lift_b<T>(v[rr], tw);
+                lift_b<T>(w[rr], tw);
+            }
+#pragma unroll
+            for (int rr = 0; rr < YB; ++rr)
+                st2((rr < HR / YA ? r0 : r1) + YA * (rr % (HR / YA)) * PITCH, v[rr], w[rr]);
+        }
+        if (more) issue(i + 1, 0, 2, 3);
+        __syncthreads();
+        // P3b: inverse y first stage -> potential factor -> forward y first
+        // stage in registers; rows YA ii + kk lie in one half buffer
+        {
+            const int p0 = (t % (NX / 2)) * 2, ii = t / (NX / 2);
+            C2 *rb = (ii < HR / YA ? b0 : b1) + ((YA * ii) % HR) * PITCH + p0;
+            C2 v[2][YA];
+            sfor<YA>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                ld2(rb + kk * PITCH, v[0][brev(kk, YA)], v[1][brev(kk, YA)]);
+            });
+            dft_inv<YA, 0, 1, T>(v[0]);
+            dft_inv<YA, 0, 1, T>(v[1]);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const T hx = ht[p0 + c];
+#pragma unroll
+                for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], fmadd(gt[ii + YB * rr], hx, thz), tier);
+            }
+            dft_fwd<YA, 0, 1, T>(v[0]);
+            dft_fwd<YA, 0, 1, T>(v[1]);
+            sfor<YA>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                st2(rb + kk * PITCH, v[0][brev(kk, YA)], v[1][brev(kk, YA)]);
+            });
+        }
+        if (more) issue(i + 1, 0, 3, 4);
+        cp_async_commit();
+        __syncthreads();
+        // P3c: forward y, last stage (radix YB), in place
+        {
+            const int p = (t % (NX / 2)) * 2, ii = t / (NX / 2);
+            C2 *r0 = b0 + ii * PITCH + p, *r1 = b1 + ii * PITCH + p;
+            C2 v[YB], w[YB];
+#pragma unroll
+            for (int rr = 0; rr < YB; ++rr)
+                ld2((rr < HR / YA ? r0 : r1) + YA * (rr % (HR / YA)) * PITCH, v[rr], w[rr]);
+#pragma unroll
+            for (int rr = 1; rr < YB; ++rr) {
+                const Lift<T> tw = wy[ii * rr];
+                lift_f<T>(v[rr], tw);
+                lift_f<T>(w[rr], tw);
+            }
+            dft_fwd<YB, 0, 1, T>(v);
+            dft_fwd<YB, 0, 1, T>(w);
+            sfor<YB>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                st2((kk < HR / YA ? r0 : r1) + YA * (kk % (HR / YA)) * PITCH, v[brev(kk, YB)],
+                    w[brev(kk, YB)]);
+            });
+        }
+        __syncthreads();
+        // P4: forward x, first stage (radix RA), in place on block j
+        {
+            const int rw = t % LY, j = t / LY;
+            C2 *bp = (rw < HR ? b0 : b1) + (rw % HR) * PITCH + RA * j;
+            C2 v[RA], w[RA];
+            load_pairs<RA>(bp, v);
+            dft_fwd<RA, 0, 1, T>(v);
+#pragma unroll
+            for (int kk = 0; kk < RA; ++kk) w[kk] = v[brev(kk, RA)];
+            store_pairs<RA>(bp, w);
+        }
+        __syncthreads();
+        // P5: forward x, last stage, to HBM.  The task is read back first so
+        // that the tile's first half buffer can take the next tile's second half
+        {
+            const int j = t % RA, rw = t / RA;
+            const C2 *rp = (rw < HR ? b0 : b1) + (rw % HR) * PITCH;
+            C2 v[RB];
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) v[rr] = rp[j + RA * rr];
+            __syncthreads();                     // tile i's buffers are free
+            if (more) issue(i + 1, 1, 0, NCR);
+            cp_async_commit();
+#pragma unroll
+            for (int rr = 1; rr < RB; ++rr) lift_f<T>(v[rr], wx[rr * RA + j]);
+            dft_fwd<RB, 0, 1, T>(v);
+            C2 *op = a.dst + (long long)z * g.plane + ((long long)(rw * g.P + r) << g.lgnx);
+            sfor<RB>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                op[j + RA * kk] = v[brev(kk, RB)];
+            });
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // =================================================================== Z ring
 // Persistent form of the complex64 Z pass for 1024-point lines and 16-column
 // tiles (P = 4 row classes, W = 4 columns): one CTA per SM walks over tiles
@@ -1222,6 +1456,20 @@ bool try_xy(const XYArgs<T> &a, cudaStream_t st)
     constexpr int NT = xy_threads<T>();
     const bool hot = a.flags == (XY_IN_MIXED | XY_OUT_MIXED | XY_KICK_FULL) &&
                      a.k.form == VF_PRODUCT && !a.k.imag && a.small_angle;
+    if constexpr (std::is_same<T, float>::value && NX == 256 && LY == 64 && RA == 16 && YA == 8) {
+        if (hot && a.ring && a.src == a.dst) {
+            constexpr int HB = (LY / 2) * (NX + 2);
+            const size_t rsmem = 3 * HB * sizeof(Cx<T>) + (NX + LY) * sizeof(Lift<T>);
+            static bool rcfg = false;
+            if (!rcfg) {
+                cudaFuncSetAttribute(xy_ring_kernel<NX, RA, RB, LY, YA, YB>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+                rcfg = true;
+            }
+            xy_ring_kernel<NX, RA, RB, LY, YA, YB><<<std::min(grid, sm_count()), 1024, rsmem, st>>>(a, grid);
+            return true;
+        }
+    }
     if (hot)
         xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, true, true><<<grid, xy_threads<T, true>(), smem, st>>>(a);
     else if (in && out)

@@ -108,6 +108,7 @@ template <class T> struct XYArgs {
     int flags;
     int small_angle;          // kick series tier: 0 any angle, 1 |V| dt <= 0.5, 2 (complex64) <= 0.16
     GradData gd;
+    int ring;                 // 1: the persistent ring form may be used (in place only)
 };
 
 template <class T> struct ZArgs {

@@ -381,6 +381,31 @@ def test_persistent_z_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
     assert rel(ring, ref) < 1e-6
 
 
+def test_persistent_xy_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
+    """The persistent XY pass (three 32-row half buffers, the next tile copied
+    in while the current one is transformed) runs the steady steps of
+    256-wide complex64 planes with 64-row tiles; 1024 tiles over at most 148
+    CTAs exercise the prefetch.  It must agree with the one-tile-per-CTA XY
+    pass and with the oracle."""
+    shape, box = (256, 256, 256), wl.CTAP_BOX
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=17) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    plan, V, c = guides_plan(ctap, shape, box, "c64")
+    assert plan.info()["fast_mask"] & 9 == 9
+    psi = to_dev(psi0, "c64")
+    plan.step(psi, 4, 0.0025)
+    ring = psi.cpu().numpy().astype(complex)
+    monkeypatch.setenv("CTAP_NO_RING", "1")
+    pplan, _, _ = guides_plan(ctap, shape, box, "c64")
+    assert pplan.info()["fast_mask"] & 9 == 1
+    psi = to_dev(psi0, "c64")
+    pplan.step(psi, 4, 0.0025)
+    plain = psi.cpu().numpy().astype(complex)
+    assert rel(ring, plain) < 1e-6
+    ref = oracle.step(psi0, V, box, 0.0025, 4)
+    assert rel(ring, ref) < 1e-6
+
+
 def test_ring_with_16_byte_aligned_psi(ctap):
     """The persistent Z pass moves 16-byte pieces: a psi view that is 16- but
     not 32-byte aligned (row segments then straddle 32-byte sectors) gives
