@@ -540,7 +540,8 @@ def run_ours(a):
     counts, pms = res["counts"], res["pass_ms"]
     kind = 0 if pms[0] >= pms[1] else 1
     fast = res["plan"].info()["fast_mask"]
-    name = (("xy_fast_kernel" if fast & 1 else "xy_pass_kernel") if kind == 0
+    name = (("xy_ring_kernel" if fast & 8 else ("xy_fast_kernel" if fast & 1 else "xy_pass_kernel"))
+            if kind == 0
             else ("z_ring_kernel" if fast & 4 else ("z_fast_kernel" if fast & 2 else "z_pass_kernel")))
     avg_ms = pms[kind] / max(counts[kind], 1)
     bytes_launch = 2 * N * esize       # one read and one write of psi
