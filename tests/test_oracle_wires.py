@@ -76,3 +76,38 @@ def test_wire_potential_is_scaled_field_magnitude(orc):
     y = orc.grid_axis(8, 0.5, 2.5)
     B = orc.wire_field([[x[3], y[5], orc.grid_axis(4, -1.0, 1.0)[2]]], seg, [0.1, 0.0, 0.3], K)
     assert np.isclose(V[2, 5, 3], 5.0 * np.linalg.norm(B) - 1.5, rtol=1e-14)
+
+
+def test_paper_chip_parameters_trap_height(orc):
+    """The paper's chip (Sec. III, captions of Fig. 2-3, stored with
+    citations in golden/paper_chip_parameters.json), in SI units: a long wire
+    with I = 0.1 A under B_b = 140 x 10^-4 T has its field zero at Eq. 5's
+    r0 = mu0 I/(2 pi B_b) = 1.43 um, inside the 4 um the paper simulates above
+    the chip; the reduced middle current 0.07 A lowers it by the same ratio.
+    The oracle's segment sum must put the minimum there; and the process time
+    is half a period of the 5 Hz longitudinal trap."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_chip_parameters.json")
+    p = json.load(open(path))
+    k = p["mu0_over_4pi_SI"]["value"]
+    Bb = p["bias_field_T"]["value"]
+    height = p["height_above_chip_m"]["value"]
+    for key in ("wire_current_outer_A", "wire_current_middle_reduced_A"):
+        I = p[key]["value"]
+        r0 = 2 * k * I / Bb
+        assert 0.0 < r0 < height
+        seg = [[0.0, 0.0, -1.0, 0.0, 0.0, 1.0, I]]            # 2 m wire: long against um
+        ys = np.linspace(0.05e-6, height, 3951)
+        pts = np.stack([0 * ys, ys, 0 * ys], axis=1)
+        mag = np.linalg.norm(orc.wire_field(pts, seg, [Bb, 0.0, 0.0], k), axis=1)
+        assert abs(ys[np.argmin(mag)] - r0) < 1.5e-9
+        # the bias is orthogonal to the wire; B_ip along the wire only adds
+        # a constant |B| floor, the minimum stays at r0
+        Bip = p["applied_field_T"]["value"]
+        mag2 = np.linalg.norm(orc.wire_field(pts, seg, [Bb, 0.0, Bip], k), axis=1)
+        assert ys[np.argmin(mag2)] == ys[np.argmin(mag)]
+        assert abs(mag2.min() - Bip) < 1e-3 * Bip
+    assert abs(p["wire_current_middle_reduced_A"]["value"] / p["wire_current_outer_A"]["value"] - 0.7) < 1e-12
+    f = p["longitudinal_trap_hz"]["value"]
+    assert abs(0.5 / f - p["process_time_s"]["value"]) < 1e-12
