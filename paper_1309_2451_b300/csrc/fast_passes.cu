@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
     Lift<T> *wy = wx + NX;                                            // exp(-2 pi i e/LY)
     for (int e = t; e < NX + LY; e += NT)
         wx[e] = e < NX ? a.tw[g.fast_x_off + (e % RA) * (e / RA)] : a.tw[g.fast_y_off + e - NX];
-    const int flags = HOT ? XY_KICK_FULL : a.flags;
+    // hot instantiations: the steady pass (merged kick), the first pass of a
+    // run (natural in, half kick) and the last (natural out, half kick)
+    const int flags = HOT ? ((IN_MIXED && OUT_MIXED) ? XY_KICK_FULL : XY_KICK_HALF) : a.flags;
     const Kick<T> &k = a.k;
     const bool kick = (flags & (XY_KICK_HALF | XY_KICK_FULL | XY_KICK_SPLIT)) != 0;
     const bool full = (flags & XY_KICK_FULL) != 0;
@@ -1450,6 +1452,10 @@ bool try_xy(const XYArgs<T> &a, cudaStream_t st)
         cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, false, false>, attr, sz);
         cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, true, false>, attr, sz);
         cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, false, false>, attr, sz);
+        if constexpr (sizeof(T) == 4) {
+            cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, true, true>, attr, sz);
+            cudaFuncSetAttribute(xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, false, true>, attr, sz);
+        }
         cfg = true;
     }
     const int grid = xy_grid(a.g);
@@ -1467,6 +1473,17 @@ bool try_xy(const XYArgs<T> &a, cudaStream_t st)
                 rcfg = true;
             }
             xy_ring_kernel<NX, RA, RB, LY, YA, YB><<<std::min(grid, sm_count()), 1024, rsmem, st>>>(a, grid);
+            return true;
+        }
+    }
+    if constexpr (sizeof(T) == 4) {
+        const bool hot_kick = a.k.form == VF_PRODUCT && !a.k.imag && a.small_angle;
+        if (hot_kick && a.flags == (XY_KICK_HALF | XY_OUT_MIXED)) {
+            xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, false, true, true><<<grid, xy_threads<T, true>(), smem, st>>>(a);
+            return true;
+        }
+        if (hot_kick && a.flags == (XY_IN_MIXED | XY_KICK_HALF)) {
+            xy_fast_kernel<T, NX, RA, RB, LY, YA, YB, true, false, true><<<grid, xy_threads<T, true>(), smem, st>>>(a);
             return true;
         }
     }
