@@ -1380,17 +1380,17 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
         __syncthreads();
 
         // Z5: the whole tile is read back to registers first (R5 rounds of
-        // 4 x 16 bytes per thread; the cross twiddles too), so every ring
-        // slot is free before the stores start: the next tile's second half
+        // 4 x 16 bytes per thread; the cross twiddles too), so its ring
+        // slots are free before the stores start: the next tile's second half
         // is copied in while this tile's inverse cross DFTs and stores run,
         // and no store waits for registers a later load would overwrite.
         // Two lanes write the two halves of each 32-byte row segment in the
         // same instruction (16 sectors per warp store: measured to drain
         // faster per SM than one lane per segment with 256-bit stores).
         constexpr int R5 = NZ * (W / 2) / NT;
+        static_assert(R5 * NT == NCH * CHZ * (W / 2), "round m reads chunk m * NCH / R5 on");
         C2 v[R5][2][P];
-#pragma unroll
-        for (int m = 0; m < R5; ++m) {
+        auto read_back = [&](int m) {
             const int q = m * NT + t;
             const int xo = (q % (W / 2)) * 2, zz = q / (W / 2);
             sfor<P>([&](auto kc) {
@@ -1399,13 +1399,19 @@ __global__ void __launch_bounds__(NT, 1) z_ring_kernel(const ZArgs<float> a, int
                 v[m][0][brev(k2, P)] = make_float2(w4.x, w4.y);
                 v[m][1][brev(k2, P)] = make_float2(w4.z, w4.w);
             });
-        }
+        };
+        // the next tile's second half goes to this tile's first-half slots:
+        // only those must be read back before it is issued
+#pragma unroll
+        for (int m = 0; m < R5 / 2; ++m) read_back(m);
         Lift<T> cw[P];
 #pragma unroll
         for (int rr = 1; rr < P; ++rr) cw[rr] = tb[W + P + rr];
-        __syncthreads();                         // tile i's chunks and tables are free
+        __syncthreads();                         // tile i's first half and tables are free
         if (i + 1 < nmine) issue(i + 1, NCH / 2, NCH);
         cp_async_commit();
+#pragma unroll
+        for (int m = R5 / 2; m < R5; ++m) read_back(m);
 #pragma unroll
         for (int m = 0; m < R5; ++m) {
             const int q = m * NT + t;
