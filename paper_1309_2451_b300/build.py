@@ -28,10 +28,38 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _compile(src, obj, extra, verbose):
+    cmd = ["nvcc", *ARCH, *FLAGS, *extra, "-c", "-o", obj, src]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    return obj
+
+
 def build(force=False, verbose=False, extra=()):
+    """Compile the csrc/*.cu files whose objects are out of date in parallel
+    (one nvcc per file; the largest file bounds the wall time), then link
+    libctap.so."""
     if not force and not _stale():
         return LIB
-    cmd = ["nvcc", *ARCH, *FLAGS, *extra, "-shared", "-o", LIB + ".tmp", *sources()]
+    from concurrent.futures import ThreadPoolExecutor
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    srcs = sources()
+    objs = [os.path.join(objdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.hpp")) + \
+        [os.path.join(ROOT, "include", "ctap.h")]
+    newest_header = max(os.path.getmtime(h) for h in headers)
+
+    def stale(src, obj):
+        return force or extra or not os.path.exists(obj) or \
+            os.path.getmtime(obj) < max(os.path.getmtime(src), newest_header)
+
+    todo = [(s, o) for s, o in zip(srcs, objs) if stale(s, o)]
+    if todo:
+        with ThreadPoolExecutor(max_workers=len(todo)) as ex:
+            list(ex.map(lambda so: _compile(so[0], so[1], extra, verbose), todo))
+    cmd = ["nvcc", *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
