@@ -29,7 +29,7 @@ constexpr int kMaxBlocks = 8192;         // => at most 2^27 elements per call
 constexpr int kThreads = 256;
 constexpr int kMaxDevices = 64;
 
-__device__ __align__(256) double g_noalloc_partials[kMaxBlocks];
+static __device__ __align__(256) double g_noalloc_partials[kMaxBlocks];
 
 // Host-side device address of g_noalloc_partials, one per device.  In host
 // code the symbol itself is only a stand-in and must never reach a kernel.
