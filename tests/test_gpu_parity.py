@@ -498,15 +498,18 @@ def test_misaligned_psi_uses_generic_passes(ctap):
 @pytest.mark.slow
 def test_full_size_c64_one_step_and_invariants(ctap):
     """256x256x1024 complex64 in the launch configuration bench.py times:
-    one step element-wise against the oracle, then norm conservation and
-    time reversibility over 20 steps (properties that hold at any size)."""
+    three steps (prologue XY, the persistent Z and XY passes of the steady
+    step, epilogue XY) element-wise against the oracle, then norm
+    conservation and time reversibility over 20 steps (properties that hold
+    at any size)."""
     shape, box = (1024, 256, 256), wl.CTAP_BOX
     plan, V, c = guides_plan(ctap, shape, box, "c64")
+    assert plan.info()["fast_mask"] & 12 == 12, plan.info()    # both ring passes
     psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=11) \
         * np.exp(2j * wl.mesh(shape, box)[2])
     psi = to_dev(psi0, "c64")
-    plan.step(psi, 1, 0.0025)
-    ref = oracle.step(psi0, V, box, 0.0025, 1)
+    plan.step(psi, 3, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, 3)
     assert rel(psi.cpu().numpy().astype(complex), ref) < 1e-6
     del ref
     n0 = plan.observables(psi)[0]
@@ -515,3 +518,21 @@ def test_full_size_c64_one_step_and_invariants(ctap):
     assert abs(plan.observables(psi)[0] / n0 - 1.0) < 1e-6
     plan.step(psi, 20, -0.0025)
     assert rel(psi.cpu().numpy().astype(complex), start.cpu().numpy().astype(complex)) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c128df"])
+def test_full_size_fp64_paths_match_oracle(ctap, dtype):
+    """The FP64 (complex128) and double-float paths at the bench size,
+    256x256x1024: two steps element-wise against the oracle at the FP64
+    parity bound."""
+    shape, box = (1024, 256, 256), wl.CTAP_BOX
+    plan, V, c = guides_plan(ctap, shape, box, dtype)
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=12) \
+        * np.exp(2j * wl.mesh(shape, box)[2])
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 2, 0.0025)
+    got = psi.cpu().numpy()
+    del psi
+    plan.close()
+    ref = oracle.step(psi0, V, box, 0.0025, 2)
+    assert rel(got, ref) < 1e-12
