@@ -164,21 +164,23 @@ def test_ctap_c64_1000_steps_accuracy_and_norm(ctap):
 
 
 # ----------------------------------------------------------- imaginary time
+@pytest.mark.parametrize("n", [128, 256])
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 2e-6)])
-def test_imaginary_time_guide_ground_state(ctap, dtype, tol):
+def test_imaginary_time_guide_ground_state(ctap, dtype, tol, n):
     """The transverse prep of the guide workloads: nz = 1 plane with guide 1
-    only, 200 imaginary-time steps at dtau = 0.01, renormalised each step."""
-    shape, box = (1, 128, 128), wl.CTAP_BOX
+    only, 200 imaginary-time steps at dtau = 0.01, renormalised each step
+    (n = 256: the plane of the 256x256x1024 workload)."""
+    shape, box = (1, n, n), wl.CTAP_BOX
     xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
     plan = ctap.Plan(shape, box, dtype)
     # guide 1 alone, V = -V0 exp(-y^2/2) exp(-(x - x1)^2/2), in product form
-    y = wl.axis(128, box[2], box[3])
-    x = wl.axis(128, box[0], box[1])
+    y = wl.axis(n, box[2], box[3])
+    x = wl.axis(n, box[0], box[1])
     gy = np.exp(-y ** 2 / 2)
     H = -wl.V0 * np.exp(-(x - xc) ** 2 / 2)[None, :]
     plan.set_potential_product(gy, H)
     V = gy[None, :, None] * H[:, None, :]
-    psi0 = wl.guide_seed_2d((128, 128), box, xc)
+    psi0 = wl.guide_seed_2d((n, n), box, xc)
     psi = to_dev(psi0, dtype)
     plan.step(psi, 200, 0.01, imag=True)
     ref = oracle.step(psi0, V, box, 0.01, 200, imag=True)
@@ -510,8 +512,16 @@ def test_full_size_c64_one_step_and_invariants(ctap):
     psi = to_dev(psi0, "c64")
     plan.step(psi, 3, 0.0025)
     ref = oracle.step(psi0, V, box, 0.0025, 3)
-    assert rel(psi.cpu().numpy().astype(complex), ref) < 1e-6
+    got = psi.cpu().numpy().astype(complex)
+    assert rel(got, ref) < 1e-6
     del ref
+    # the FP64 reductions of the bench's observation step, and the
+    # y-integrated density, on the same full-size state
+    obs = plan.observables(psi)
+    want = oracle.observables(got, V, box, c, wl.POP_HALFWIDTH)
+    assert np.allclose(obs, want, rtol=1e-6, atol=1e-9), (obs, want)
+    assert np.allclose(plan.density_xz(psi), oracle.density_xz(got, box), rtol=1e-12, atol=1e-300)
+    del got
     n0 = plan.observables(psi)[0]
     start = psi.clone()
     plan.step(psi, 20, 0.0025)
