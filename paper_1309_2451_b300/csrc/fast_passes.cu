@@ -277,6 +277,12 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
     __shared__ T gtab[LY];              // g(y), y = r + P jy
     __shared__ T htab[NX];              // H(x, z) tau at swapped position
     __shared__ Lift<T> ytab[LY];        // separable y factor
+    // complex64 observables: per-CTA tables so that the per-point work is FP32
+    // only (g(y) of the tile's rows and H(x, z) rounded to FP32 as before;
+    // guide membership of each column decided once, in FP64)
+    __shared__ float obs_g[sizeof(T) == 4 ? LY : 1];
+    __shared__ float obs_h[sizeof(T) == 4 ? NX : 1];
+    __shared__ unsigned char obs_in[sizeof(T) == 4 ? NX : 1];
 
     const Geom &g = a.g;
     const int t = threadIdx.x;
@@ -307,6 +313,22 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
     auto unswx = [](int p) { return p / RA + RB * (p % RA); };   // position -> natural x
     auto swy = [](int jy) { return YA * (jy % YB) + jy / YB; };
 
+    if constexpr (sizeof(T) == 4 && !HOT) {
+        if (flags & XY_RED_OBS) {
+            if (t < LY && a.vform_obs == VF_PRODUCT) obs_g[t] = (float)a.rd.g64[r + t * g.P];
+            if (t < NX) {
+                const double xq = g.box[0] + (double)t * g.dx;
+                unsigned m = 0;
+                if (a.rd.xc) {
+                    m |= fabs(xq - a.rd.xc[zl]) < a.rd.hw ? 1u : 0u;
+                    m |= fabs(xq - a.rd.xc[g.nz + zl]) < a.rd.hw ? 2u : 0u;
+                    m |= fabs(xq - a.rd.xc[2 * g.nz + zl]) < a.rd.hw ? 4u : 0u;
+                }
+                obs_in[t] = (unsigned char)m;
+                obs_h[t] = (a.vform_obs == VF_PRODUCT) ? (float)a.rd.H64[(long long)z * g.nx + t] : 0.0f;
+            }
+        }
+    }
     if (t < LY) {
         const int y = r + t * g.P;
         if (HOT || k.form == VF_PRODUCT) gtab[t] = k.g[y];
@@ -447,15 +469,6 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
             for (int c = 0; c < 2; ++c) {
                 const int p = p0 + c, x = unswx(p);
                 if (!HOT && (flags & XY_RED_OBS)) {
-                    const double xq = g.box[0] + (double)x * g.dx;
-                    bool in0 = false, in1 = false, in2 = false;
-                    if (a.rd.xc) {
-                        in0 = fabs(xq - a.rd.xc[zl]) < a.rd.hw;
-                        in1 = fabs(xq - a.rd.xc[g.nz + zl]) < a.rd.hw;
-                        in2 = fabs(xq - a.rd.xc[2 * g.nz + zl]) < a.rd.hw;
-                    }
-                    const double hz =
-                        (a.vform_obs == VF_PRODUCT) ? a.rd.H64[(long long)z * g.nx + x] : 0.0;
                     const double vz64 = a.rd.vz64 ? a.rd.vz64[zl] : 0.0;
                     const double vxz = (a.vform_obs == VF_SEPARABLE)
                                            ? a.rd.Vsep[x] + a.rd.Vsep[g.nx + g.ny + zl] : 0.0;
@@ -463,6 +476,8 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                         // complex64: products and the column's YA-term partial sums in
                         // FP32 (the data carry 24 bits), FP64 from there on; FP64
                         // arithmetic per point would bind this pass to B300's FP64 rate
+                        const float hz32 = obs_h[x], vz32 = (float)vz64;
+                        const unsigned m = obs_in[x];
                         float sd = 0.0f, svd = 0.0f;
 #pragma unroll
                         for (int rr = 0; rr < YA; ++rr) {
@@ -471,17 +486,29 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                             const float d = fmadd(u.x, u.x, u.y * u.y);
                             float V = 0.0f;
                             if (a.vform_obs == VF_DENSE) V = k.Vd[pbase + ((long long)y << g.lgnx) + x];
-                            else if (a.vform_obs == VF_PRODUCT) V = (float)a.rd.g64[y] * (float)hz + (float)vz64;
+                            else if (a.vform_obs == VF_PRODUCT) V = fmadd(obs_g[jy], hz32, vz32);
                             else if (a.vform_obs == VF_SEPARABLE) V = (float)(vxz + a.rd.Vsep[g.nx + y]);
                             sd += d;
                             svd = fmadd(V, d, svd);
                         }
                         acc[0] += sd;
                         acc[1] += svd;
-                        acc[2] += in0 ? (double)sd : 0.0;
-                        acc[3] += in1 ? (double)sd : 0.0;
-                        acc[4] += in2 ? (double)sd : 0.0;
+                        if (m) {
+                            const double sdd = (double)sd;
+                            acc[2] += (m & 1u) ? sdd : 0.0;
+                            acc[3] += (m & 2u) ? sdd : 0.0;
+                            acc[4] += (m & 4u) ? sdd : 0.0;
+                        }
                     } else {
+                        const double xq = g.box[0] + (double)x * g.dx;
+                        bool in0 = false, in1 = false, in2 = false;
+                        if (a.rd.xc) {
+                            in0 = fabs(xq - a.rd.xc[zl]) < a.rd.hw;
+                            in1 = fabs(xq - a.rd.xc[g.nz + zl]) < a.rd.hw;
+                            in2 = fabs(xq - a.rd.xc[2 * g.nz + zl]) < a.rd.hw;
+                        }
+                        const double hz =
+                            (a.vform_obs == VF_PRODUCT) ? a.rd.H64[(long long)z * g.nx + x] : 0.0;
 #pragma unroll
                         for (int rr = 0; rr < YA; ++rr) {
                             const int y = r + (i + YB * rr) * g.P;
