@@ -19,15 +19,6 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale():
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        glob.glob(os.path.join(CSRC, "*.hpp")) + [os.path.join(ROOT, "include", "ctap.h")]
-    return any(os.path.getmtime(d) > t for d in deps)
-
-
 def _compile(src, obj, extra, verbose):
     cmd = ["nvcc", *ARCH, *FLAGS, *extra, "-c", "-o", obj, src]
     if verbose:
@@ -40,25 +31,36 @@ def build(force=False, verbose=False, extra=()):
     """Compile the csrc/*.cu files whose objects are out of date in parallel
     (one nvcc per file; the largest file bounds the wall time), then link
     libctap.so."""
-    if not force and not _stale():
-        return LIB
     from concurrent.futures import ThreadPoolExecutor
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
     srcs = sources()
     objs = [os.path.join(objdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.hpp")) + \
-        [os.path.join(ROOT, "include", "ctap.h")]
-    newest_header = max(os.path.getmtime(h) for h in headers)
+    def deps(path, seen):
+        """path and every file it includes with #include "..." (recursively)."""
+        if path in seen or not os.path.exists(path):
+            return seen
+        seen.add(path)
+        with open(path, errors="replace") as f:
+            for line in f:
+                line = line.strip()
+                if line.startswith("#include") and '"' in line:
+                    inc = line.split('"')[1]
+                    deps(os.path.normpath(os.path.join(os.path.dirname(path), inc)), seen)
+        return seen
 
     def stale(src, obj):
-        return force or extra or not os.path.exists(obj) or \
-            os.path.getmtime(obj) < max(os.path.getmtime(src), newest_header)
+        if force or extra or not os.path.exists(obj):
+            return True
+        t = os.path.getmtime(obj)
+        return any(os.path.getmtime(d) > t for d in deps(src, set()))
 
     todo = [(s, o) for s, o in zip(srcs, objs) if stale(s, o)]
     if todo:
         with ThreadPoolExecutor(max_workers=len(todo)) as ex:
             list(ex.map(lambda so: _compile(so[0], so[1], extra, verbose), todo))
+    elif os.path.exists(LIB) and all(os.path.getmtime(o) <= os.path.getmtime(LIB) for o in objs):
+        return LIB
     cmd = ["nvcc", *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd))

@@ -77,16 +77,26 @@ __global__ void __launch_bounds__(kThreads) norm_finish_kernel(const double *par
     if (threadIdx.x == 0) *out = t * dV;
 }
 
-// One-time look-up of the array's device address on the current device.
-ctap_status partials_address(double **addr)
+// Device address of the array on the current device.  Outside stream
+// capture it is looked up again on every call (the query is cheap and
+// allocates nothing), so a context that was torn down and recreated -- a
+// cudaDeviceReset, say -- never leaves a stale address behind.  During
+// capture the address found by the last call outside capture on this
+// device is used; with none yet the call fails.
+ctap_status partials_address(cudaStream_t st, double **addr)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return CTAP_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return CTAP_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -94,6 +104,7 @@ ctap_status partials_address(double **addr)
         }
         g_partials_addr[dev] = static_cast<double *>(p);
     }
+    if (!g_partials_addr[dev]) return CTAP_ERR_CUDA;
     *addr = g_partials_addr[dev];
     return CTAP_OK;
 }
@@ -107,10 +118,10 @@ extern "C" ctap_status ctap_norm_noalloc(const void *psi, long long n, ctap_dtyp
     if (dtype != CTAP_C64 && dtype != CTAP_C128) return CTAP_ERR_DTYPE;
     const long long nblk = (n + kChunk - 1) / kChunk;
     if (nblk > kMaxBlocks) return CTAP_ERR_UNSUPPORTED_SIZE;   // n > CTAP_NOALLOC_MAX_ELEMENTS
-    double *partials = nullptr;
-    ctap_status s = partials_address(&partials);
-    if (s != CTAP_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double *partials = nullptr;
+    ctap_status s = partials_address(st, &partials);
+    if (s != CTAP_OK) return s;
     if (dtype == CTAP_C64)
         norm_partials_kernel<float2><<<(int)nblk, kThreads, 0, st>>>(
             static_cast<const float2 *>(psi), n, partials);
