@@ -228,9 +228,12 @@ ctap_status ctap_pass_times(ctap_plan_t plan, long long counts[3], double ms[3])
 /* Pass geometry chosen for the plan: info[0] = P (row classes per plane),
  * info[1] = rows per XY tile, info[2] = columns per Z tile, info[3] = bytes
  * of one psi, info[4] = fast-pass mask (1: specialised XY pass, 2:
- * specialised Z pass, 4: the in-place Z pass runs as the persistent ring
- * kernel, 8: the steady in-place XY pass runs as the persistent ring
- * kernel). */
+ * specialised Z pass, 4: the in-place Z pass runs as a persistent ring
+ * kernel, 8: the steady in-place XY pass runs as a persistent ring kernel,
+ * 16: the real-time Z ring runs in packed FP32-pair arithmetic, 32: the
+ * steady XY ring runs in packed FP32-pair arithmetic).  CTAP_NO_PACKED=1 in
+ * the environment at plan creation keeps the scalar ring kernels,
+ * CTAP_NO_RING=1 the one-tile-per-CTA passes. */
 ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);
 
 /* Largest element count ctap_norm_noalloc accepts (2^27). */
@@ -247,10 +250,13 @@ ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);
  *   out: DEVICE pointer to one double, caller-owned, written
  *        asynchronously on cuda_stream (NULL = legacy default stream).
  * FP64 partial sums go to a fixed 64 KiB file-scope device array that
- * every GPU loading the library holds until the process exits.  The first
- * call on each device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the array: calls that
+ * every GPU loading the library holds until the process exits.  Each call
+ * made outside stream capture looks up that array's device address
+ * (cudaGetSymbolAddress) on the current device, so the address stays valid
+ * across a device reset; a call made during capture reuses the address of
+ * the last call outside capture on that device, so make one call on each
+ * device before any stream capture (a captured call with none fails with
+ * CTAP_ERR_CUDA).  All calls share the array: calls that
  * overlap on the GPU (other streams or host threads) race on it, calls on
  * one stream are ordered.  Every slot a call reads is written by the same
  * call, so nothing needs clearing in between.

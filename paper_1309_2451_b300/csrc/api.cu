@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -13,6 +14,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "packed_passes.cuh"
 #include "plan.hpp"
 
 using namespace ctap;
@@ -164,6 +166,7 @@ void drop_caches(PlanState &st)
     for (auto &t : st.tabsets) {
         dev_free(t.kin);
         dev_free(t.sep);
+        dev_free(t.kin_xy);
     }
     st.tabsets.clear();
 }
@@ -172,6 +175,13 @@ void invalidate_sep(PlanState &st)
 {
     drop_graphs(st);
     for (auto &t : st.tabsets) t.sep_valid = false;
+}
+
+// the packed persistent Z pass applies to this plan's steady real-time steps
+bool packed_z_on(const PlanState &st)
+{
+    return st.fast_z && !st.no_ring && !st.no_packed && st.dtype == CTAP_C64 &&
+           packed_z_supported(st.geom);
 }
 
 ctap_status get_tables(PlanState &st, double dt, int imag, TabSet **out)
@@ -185,6 +195,7 @@ ctap_status get_tables(PlanState &st, double dt, int imag, TabSet **out)
         if (c.size() >= 4) {
             dev_free(c.front().kin);
             dev_free(c.front().sep);
+            dev_free(c.front().kin_xy);
             c.erase(c.begin());
         }
         c.push_back(TabSet{dt, imag, nullptr, nullptr, false});
@@ -192,6 +203,10 @@ ctap_status get_tables(PlanState &st, double dt, int imag, TabSet **out)
         std::vector<unsigned char> h;
         build_kinetic(st, dt, imag, h);
         CTAP_TRY(upload(st, &hit->kin, nullptr, h.data(), h.size()));
+        if (packed_z_on(st) && !imag) {
+            build_kinetic_xy(st, dt, h);
+            CTAP_TRY(upload(st, &hit->kin_xy, nullptr, h.data(), h.size()));
+        }
     }
     if (st.vform == VF_SEPARABLE && !hit->sep_valid) {
         std::vector<unsigned char> h;
@@ -248,6 +263,7 @@ template <class T> ZArgs<T> z_args(PlanState &st, const TabSet *ts, int imag)
     a.g = st.geom;
     a.tw = reinterpret_cast<const Lift<T> *>(st.d_tw);
     a.kin = ts ? reinterpret_cast<const Lift<T> *>(ts->kin) : nullptr;
+    a.kin_xy = ts ? ts->kin_xy : nullptr;
     a.imag = imag;
     a.inv_n = (T)(1.0 / (double)st.Nrep);      // transforms act on one replica
     a.k2h = st.d_k2h;
@@ -265,7 +281,10 @@ template <class T> ctap_status go_xy(PlanState &st, const XYArgs<T> &a)
     bool done = false;
     // the fast XY pass moves two values per 16-byte access
     const bool aligned = ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15) == 0;
-    if (st.fast_xy && aligned) done = launch_xy_fast(a, st.stream);
+    if constexpr (std::is_same<T, float>::value) {
+        if (st.fast_xy && aligned && !st.no_packed) done = launch_xy_packed(a, st.stream);
+    }
+    if (!done && st.fast_xy && aligned) done = launch_xy_fast(a, st.stream);
     if (!done) launch_xy<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "xy pass");
@@ -278,7 +297,10 @@ template <class T> ctap_status go_z(PlanState &st, const ZArgs<T> &a)
     bool done = false;
     // the fast Z pass moves two columns per 16-byte access
     const bool aligned = ((reinterpret_cast<uintptr_t>(a.src) | reinterpret_cast<uintptr_t>(a.dst)) & 15) == 0;
-    if (st.fast_z && aligned) done = launch_z_fast(a, st.stream);
+    if constexpr (std::is_same<T, float>::value) {
+        if (st.fast_z && aligned && !st.no_packed) done = launch_z_packed(a, st.stream);
+    }
+    if (!done && st.fast_z && aligned) done = launch_z_fast(a, st.stream);
     if (!done) launch_z<T>(a, st.stream);
     prof_end(st, ev);
     return post_launch(st, "z pass");
@@ -557,6 +579,20 @@ ctap_status run_adjoint(PlanState &st, const Cx<T> *psi0, int nsteps, double dt,
             dev_free(acc);
         }
     } b;
+    // nseg checkpoints + one segment of Kseg states + two working states:
+    // refuse before allocating when that cannot fit in the free device memory
+    {
+        size_t freeb = 0, totalb = 0;
+        const double need = (double)bytes * (double)(nseg + Kseg + 2) + 16.0 * nacc;
+        if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess && need > 0.95 * (double)freeb) {
+            char msg[160];
+            std::snprintf(msg, sizeof msg,
+                          "adjoint needs %.1f GB of checkpoints and segment states, %.1f GB "
+                          "free; use a larger K or fewer steps",
+                          need / 1e9, (double)freeb / 1e9);
+            return fail(st, CTAP_ERR_OOM, msg);
+        }
+    }
     CTAP_TRY(dev_alloc(st, &b.cp, bytes * nseg));
     CTAP_TRY(dev_alloc(st, &b.seg, bytes * Kseg));
     CTAP_TRY(dev_alloc(st, &b.work, bytes));
@@ -835,6 +871,8 @@ ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const do
     st.force_generic = fg && fg[0] == '1';
     const char *nr = std::getenv("CTAP_NO_RING");
     st.no_ring = nr && nr[0] == '1';
+    const char *npk = std::getenv("CTAP_NO_PACKED");
+    st.no_packed = npk && npk[0] == '1';
     try {
         build_geometry(st, emax, maxv);
     } catch (const std::exception &) {
@@ -1257,7 +1295,9 @@ ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5])
                       st->geom.P == 4 && st->geom.w == 4;
     const bool xy_ring = st->fast_xy && !st->no_ring && st->dtype == CTAP_C64 && st->nx == 256 &&
                          st->geom.Ly == 64;
-    info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0) | (ring ? 4 : 0) | (xy_ring ? 8 : 0);
+    const bool xy_packed = xy_ring && !st->no_packed && packed_xy_supported(st->geom);
+    info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0) | (ring ? 4 : 0) | (xy_ring ? 8 : 0) |
+              (packed_z_on(*st) ? 16 : 0) | (xy_packed ? 32 : 0);
     return CTAP_OK;
 }
 

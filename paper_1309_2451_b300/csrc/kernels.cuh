@@ -124,6 +124,7 @@ template <class T> struct ZArgs {
     double *partials;
     int observe;              // 1: forward only, reduce sum k^2/2 |psi_k|^2, no store
     int ring;                 // 1: the persistent ring form may be used (in place only)
+    const void *kin_xy;       // Lift<T> of exp(-i (kx^2 + ky^2) dt/2) [ny][nx], or null
 };
 
 template <class T> void launch_xy(const XYArgs<T> &a, cudaStream_t st);

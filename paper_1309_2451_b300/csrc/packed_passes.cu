@@ -1,0 +1,854 @@
+// packed_passes.cu -- the steady complex64 passes in packed FP32 arithmetic.
+//
+// B300 (the sm_100 family) issues one instruction for a PAIR of FP32 adds,
+// multiplies or fused multiply-adds (add/mul/fma.rn.f32x2): twice the FP32
+// work per issue slot of the scalar forms, at the same FP32 pipe rate.  The
+// specialised passes in fast_passes.cu are bound by instruction issue and
+// shared-memory traffic, not by HBM, so the passes here hold the values of
+// TWO transform lines per thread in structure-of-arrays form -- one FP32
+// pair for the real parts, one for the imaginary parts -- and run every
+// butterfly, lifted rotation and scaling on both lines with one packed
+// instruction.  The multiplications by +-i inside the radix-2 butterflies
+// become free (a swap of the two pairs and a choice of add or subtract).
+//
+// Same mathematics, HBM layout, tables and lifting scheme as the other
+// passes (mixed representation between passes: natural kx, natural k',
+// rows j P + r; every twiddle a three-shear rotation), so plans mix them
+// freely; the results differ from the scalar passes by FP32 rounding only.
+//
+// Z pass (z_pk_kernel, complex64, nz = 1024, 16-column tiles of P = 4 row
+// classes x W = 4 columns; the geometry of 256 x 256 planes):
+//   z = 256 a + 16 b + c, kz = k0 + 4 k1 + 64 k2 (decimation in frequency)
+//   A   cross twiddle + P-point DFT over the row classes (finishes ky), the
+//       kinetic rotation of the column's (kx, ky) (constant along z), the
+//       radix-4 DFT over a and the twiddle exp(-2 pi i b k0/64);
+//   B   radix-16 DFT over b and the twiddle exp(-2 pi i c (k0 + 4 k1)/1024);
+//   C   radix-16 DFT over c, the kz kinetic rotation with the sign, 1/N and
+//       the (kx, ky) sign, then the exact mirror back;
+//   B'  mirror of B;  A'  mirror of A (without the kinetic rotation), and
+//       16-byte streaming stores.
+// Each twiddle layer sits at the end of the phase that produces its inputs
+// (and at the start of the mirror phase): the radix-4 phase needs only
+// three table entries per task, and the middle phase none.
+// A thread holds 16 values of each of two adjacent tile columns (32 complex
+// values, 64 registers); 512 threads cover a tile per phase, 16 warps per
+// SM.  The tile lives in the same ring of 128-row chunks as z_ring_kernel
+// and the next tile's copies are issued between phases.
+#include <algorithm>
+#include <cstdlib>
+
+#include "packed_passes.cuh"
+
+namespace ctap {
+
+namespace {
+
+// ------------------------------------------------------------ pair arithmetic
+__device__ __forceinline__ float2 pk(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// Two complex values (one from each of two lines): x = (re_a, re_b),
+// y = (im_a, im_b).
+struct Q {
+    float2 x, y;
+};
+
+__device__ __forceinline__ Q qadd(const Q &a, const Q &b) { return Q{add2(a.x, b.x), add2(a.y, b.y)}; }
+__device__ __forceinline__ Q qsub(const Q &a, const Q &b) { return Q{sub2(a.x, b.x), sub2(a.y, b.y)}; }
+
+// rotation of both values by the angles whose lifting coefficients are the
+// pairs p = -tan(phi/2), u = sin(phi); qrot_b is its exact mirror
+__device__ __forceinline__ void qrot_f(Q &v, float2 p, float2 u)
+{
+    v.x = fma2(p, v.y, v.x);
+    v.y = fma2(u, v.x, v.y);
+    v.x = fma2(p, v.y, v.x);
+}
+__device__ __forceinline__ void qrot_b(Q &v, float2 p, float2 u)
+{
+    const float2 mp = neg2(p), mu = neg2(u);
+    v.x = fma2(mp, v.y, v.x);
+    v.y = fma2(mu, v.x, v.y);
+    v.x = fma2(mp, v.y, v.x);
+}
+__device__ __forceinline__ void qscale(Q &v, float2 s)
+{
+    v.x = mul2(s, v.x);
+    v.y = mul2(s, v.y);
+}
+// a table twiddle (the same for both lines): s * rotate(phi), and its mirror
+__device__ __forceinline__ void qlift_f(Q &v, const Lift<float> &w)
+{
+    qrot_f(v, pk(w.p), pk(w.u));
+    qscale(v, pk(w.s));
+}
+__device__ __forceinline__ void qlift_b(Q &v, const Lift<float> &w)
+{
+    qscale(v, pk(w.s));
+    qrot_b(v, pk(w.p), pk(w.u));
+}
+
+// Forward R-point DFT (exp(-2 pi i jk/R)) of v[OFF + k ST] on both lines,
+// radix-2 decimation in frequency with the fixed rotations of RegTw; output
+// frequency k lands in v[OFF + brev(k, R) ST].  The factor -i of a butterfly
+// is taken before its rotation (the two commute), as a swap of the pairs.
+template <int R, int OFF, int ST> __device__ __forceinline__ void qdft_fwd(Q *v)
+{
+    if constexpr (R > 1) {
+        constexpr int H = R / 2;
+        sfor<H>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            using W = RegTw<R, j>;
+            const Q a = v[OFF + j * ST], b = v[OFF + (j + H) * ST];
+            v[OFF + j * ST] = qadd(a, b);
+            Q d;
+            if constexpr (W::mode >= 2) {          // -i (a - b)
+                d.x = sub2(a.y, b.y);
+                d.y = sub2(b.x, a.x);
+            } else {
+                d = qsub(a, b);
+            }
+            if constexpr (W::mode == 1 || W::mode == 3) qrot_f(d, pk(float(W::p)), pk(float(W::u)));
+            v[OFF + (j + H) * ST] = d;
+        });
+        qdft_fwd<H, OFF, ST>(v);
+        qdft_fwd<H, OFF + H * ST, ST>(v);
+    }
+}
+
+// Exact mirror of qdft_fwd: input in bit-reversed register order, output in
+// natural order, R times the inverse DFT.
+template <int R, int OFF, int ST> __device__ __forceinline__ void qdft_inv(Q *v)
+{
+    if constexpr (R > 1) {
+        constexpr int H = R / 2;
+        qdft_inv<H, OFF, ST>(v);
+        qdft_inv<H, OFF + H * ST, ST>(v);
+        sfor<H>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            using W = RegTw<R, j>;
+            const Q a = v[OFF + j * ST];
+            Q e = v[OFF + (j + H) * ST];
+            if constexpr (W::mode == 1 || W::mode == 3) qrot_b(e, pk(float(W::p)), pk(float(W::u)));
+            if constexpr (W::mode >= 2) {          // a +- i e
+                v[OFF + j * ST] = Q{sub2(a.x, e.y), add2(a.y, e.x)};
+                v[OFF + (j + H) * ST] = Q{add2(a.x, e.y), sub2(a.y, e.x)};
+            } else {
+                v[OFF + j * ST] = qadd(a, e);
+                v[OFF + (j + H) * ST] = qsub(a, e);
+            }
+        });
+    }
+}
+
+// shared-memory pieces: 16 bytes, two adjacent columns of one tile row.
+// AoS (as copied from HBM): re0 im0 re1 im1.  SoA (after phase A): re0 re1
+// im0 im1.
+__device__ __forceinline__ Q ld_aos(const float2 *p)
+{
+    const float4 w = *reinterpret_cast<const float4 *>(p);
+    return Q{make_float2(w.x, w.z), make_float2(w.y, w.w)};
+}
+__device__ __forceinline__ Q ld_soa(const float2 *p)
+{
+    const float4 w = *reinterpret_cast<const float4 *>(p);
+    return Q{make_float2(w.x, w.y), make_float2(w.z, w.w)};
+}
+__device__ __forceinline__ void st_soa(float2 *p, const Q &v)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v.x.x, v.x.y, v.y.x, v.y.y);
+}
+
+// The thread index through an opaque move.  A mirror phase addresses the
+// same shared-memory positions (and table entries) as its forward phase;
+// taken from the plain index, the compiler keeps those values live from the
+// forward phase through every phase in between, which overflows the
+// 128-register budget of 512 threads into local memory.  The mirror phase
+// that closes the longest such span (A' in the Z pass, P3c in the XY pass)
+// takes its index through this move instead: measured no spills.
+__device__ __forceinline__ int phase_tid()
+{
+    int t;
+    asm volatile("mov.u32 %0, %1;" : "=r"(t) : "r"((int)threadIdx.x));
+    return t;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int kZpkNT = 512;        // threads of the packed Z pass
+constexpr int kZpkCHZ = 128;       // z-rows per ring chunk
+constexpr int kZpkNRING = 12;      // ring chunks (a tile is eight)
+
+}  // namespace
+
+// =============================================================== Z (packed)
+// Persistent: one CTA per SM walks over the tiles blockIdx.x + i gridDim.x.
+// kin_xy: lifted rotations of exp(-i (kx^2 + ky^2) dt/2), [ny][nx] (FP64
+// generated, rounded once).  Real time only.
+__global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, int ntiles)
+{
+    constexpr int NZ = 1024, P = 4, W = 4, C = P * W, NT = kZpkNT;
+    constexpr int CHZ = kZpkCHZ, NCH = NZ / CHZ, NRING = kZpkNRING, CHE = CHZ * C;
+    using T = float;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *ring = reinterpret_cast<float2 *>(smraw);
+    Lift<T> *wz = reinterpret_cast<Lift<T> *>(ring + NRING * CHE);   // exp(-2 pi i e/1024)
+    Lift<T> *kz = wz + NZ;                                            // kz kinetic, s/N
+    // per-tile tables, double buffered: [0..15] (kx, ky) kinetic rotation of
+    // tile column k2 W + x (x fastest), [16..18] cross twiddles r = 1..3
+    __shared__ Lift<T> tabs[2][C + P - 1];
+    const Geom &g = a.g;
+    const Lift<T> *kxy = static_cast<const Lift<T> *>(a.kin_xy);
+    const int t0 = threadIdx.x;
+    const int G = gridDim.x;
+    const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
+    const int nblk_mask = (1 << g.nblk_lg) - 1;
+
+    auto slot_of = [](int i, int c) {
+        int s = (i % 3) * NCH + c;
+        s -= (s >= NRING) ? NRING : 0;
+        s -= (s >= NRING) ? NRING : 0;
+        return s;
+    };
+    // element offset of piece q (columns 2q, 2q + 1) of z-row zz in chunk slot s
+    auto piece = [](int s, int zz, int q) { return s * CHE + (zz % CHZ) * C + 2 * (q ^ (zz & 7)); };
+
+    // asynchronous copy of chunks [c0, c1) of the i-th tile: thread t moves
+    // piece (row class r, half h) of z-rows czl + 64 m of each chunk
+    const int ch = t0 & 1, cr = (t0 >> 1) & (P - 1), czl = t0 >> 3;
+    auto issue = [&](int i, int c0, int c1) {
+        const int tile = blockIdx.x + i * G;
+        const int tl = tile & ((1 << g.lgzt) - 1);
+        const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
+        const float2 *src = a.src + (long long)(tile >> g.lgzt) * g.rstride +
+                            ((long long)(kp * P + cr) << g.lgnx) + b * W + 2 * ch +
+                            (long long)(c0 * CHZ + czl) * g.plane;
+        const long long zstep = (long long)(NT / 8) * g.plane;
+        for (int c = c0; c < c1; ++c) {
+            const int s = slot_of(i, c);
+#pragma unroll
+            for (int m = 0; m < CHZ / (NT / 8); ++m) {
+                const int zz = c * CHZ + czl + m * (NT / 8);
+                cp_async16(ring + piece(s, zz, 2 * cr + ch), src);
+                src += zstep;
+            }
+        }
+    };
+    auto load_tabs = [&](int i) {
+        if (t0 < C + P - 1) {
+            const int t = t0;
+            const int tile = blockIdx.x + i * G;
+            const int tl = tile & ((1 << g.lgzt) - 1);
+            const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
+            Lift<T> v;
+            if (t < C) {
+                const int kx = b * W + (t & (W - 1)), ky = kp + ((t / W) << g.lgLy);
+                v = kxy[((long long)ky << g.lgnx) + kx];
+            } else {
+                v = a.tw[g.cross_off + (((t - C + 1) * kp) & (g.ny - 1))];
+            }
+            tabs[i & 1][t0] = v;
+        }
+    };
+
+    if (nmine > 0) {
+        issue(0, 0, NCH);
+        load_tabs(0);
+    }
+    cp_async_commit();
+    for (int e = t0; e < NZ; e += NT) {
+        wz[e] = a.tw[g.fast_z_off + e];
+        Lift<T> k = a.kin[g.nx + g.ny + e];
+        k.s *= a.inv_n;                      // 1/N of the unnormalised transforms
+        kz[e] = k;
+    }
+
+    for (int i = 0; i < nmine; ++i) {
+        const int tile = blockIdx.x + i * G;
+        const int tl = tile & ((1 << g.lgzt) - 1);
+        const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
+        const long long colbase = (long long)(tile >> g.lgzt) * g.rstride +
+                                  ((long long)(kp * P) << g.lgnx) + b * W;
+        const bool more = i + 1 < nmine;
+        if (more) load_tabs(i + 1);
+        cp_async_wait_all();
+        __syncthreads();                               // tile i and its tables visible
+        const Lift<T> *tb = tabs[i & 1];
+        // ring slot of chunk c of tile i (computed, not indexed: a register
+        // array indexed at run time would live in local memory)
+        const int sbase = (i % 3) * NCH;
+        auto sl = [sbase](int c) { const int s = sbase + c; return s >= NRING ? s - NRING : s; };
+
+        // ---- A: cross DFT over r, (kx, ky) kinetic rotation, radix-4 over a
+        {
+            const int t = threadIdx.x;
+            const int zl = t & 255, h = t >> 8;
+            Lift<T> tw64[3];
+#pragma unroll
+            for (int k0 = 1; k0 < 4; ++k0) tw64[k0 - 1] = wz[16 * (zl >> 4) * k0];
+            Q v[4][4];                                 // [a -> k0][r -> k2y]
+#pragma unroll
+            for (int aa = 0; aa < 4; ++aa) {
+                const int zz = 256 * aa + zl;
+#pragma unroll
+                for (int r = 0; r < P; ++r) v[aa][r] = ld_aos(ring + piece(sl(zz / CHZ), zz, 2 * r + h));
+            }
+#pragma unroll
+            for (int aa = 0; aa < 4; ++aa) {
+#pragma unroll
+                for (int r = 1; r < P; ++r) qlift_f(v[aa][r], tb[C + r - 1]);
+                qdft_fwd<4, 0, 1>(v[aa]);              // v[aa][brev(k2y)]
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) {
+                const Lift<T> &l0 = tb[k2 * W + 2 * h], &l1 = tb[k2 * W + 2 * h + 1];
+                const float2 p = make_float2(l0.p, l1.p), u = make_float2(l0.u, l1.u);
+                Q col[4];
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa) {
+                    col[aa] = v[aa][brev(k2, 4)];
+                    qrot_f(col[aa], p, u);
+                }
+                qdft_fwd<4, 0, 1>(col);                // col[brev(k0)]
+#pragma unroll
+                for (int k0 = 0; k0 < 4; ++k0) {
+                    // twiddle of the next stage, exp(-2 pi i b k0/64), b = zl/16
+                    if (k0 > 0) qlift_f(col[brev(k0, 4)], tw64[k0 - 1]);
+                    const int zz = 256 * k0 + zl;
+                    st_soa(ring + piece(sl(zz / CHZ), zz, 2 * k2 + h), col[brev(k0, 4)]);
+                }
+            }
+        }
+        if (more) issue(i + 1, 0, 1);
+        __syncthreads();
+
+        // ---- B: radix-16 over b, then the twiddle of the last stage,
+        //      exp(-2 pi i c (k0 + 4 k1)/1024)
+        {
+            const int t = threadIdx.x;
+            const int q = t & 7, c = (t >> 3) & 15, k0 = t >> 7;
+            Q v[16];
+#pragma unroll
+            for (int bb = 0; bb < 16; ++bb) {
+                const int zz = 256 * k0 + 16 * bb + c;
+                v[bb] = ld_soa(ring + piece(sl(zz / CHZ), zz, q));
+            }
+            qdft_fwd<16, 0, 1>(v);
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                Q &w = v[brev(k1, 16)];
+                qlift_f(w, wz[c * (k0 + 4 * k1)]);
+                const int zz = 256 * k0 + 16 * k1 + c;
+                st_soa(ring + piece(sl(zz / CHZ), zz, q), w);
+            }
+        }
+        if (more) issue(i + 1, 1, 2);
+        __syncthreads();
+
+        // ---- C: radix-16 over c, the kz kinetic factor, and back.  A warp
+        //      spans four consecutive m (k0 fastest after the piece) so that
+        //      its kinetic table reads fall on distinct banks.
+        {
+            const int t = threadIdx.x;
+            const int q = t & 7, k0 = (t >> 3) & 3, k1 = t >> 5;
+            const int m = k0 + 4 * k1;
+            const int zr = 256 * k0 + 16 * k1;         // 16 consecutive rows, one chunk
+            const int s = sl(zr / CHZ);
+            // sign of the (kx, ky) rotation of the two columns
+            const int k2y = q >> 1, x0 = 2 * (q & 1);
+            const float2 sxy = make_float2(tb[k2y * W + x0].s, tb[k2y * W + x0 + 1].s);
+            Q v[16];
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) v[cc] = ld_soa(ring + piece(s, zr + cc, q));
+            qdft_fwd<16, 0, 1>(v);                     // v[brev(k2)]: kz = m + 64 k2
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const Lift<T> kk = kz[m + 64 * k2];
+                Q &w = v[brev(k2, 16)];
+                qrot_f(w, pk(kk.p), pk(kk.u));
+                qscale(w, mul2(sxy, pk(kk.s)));
+            }
+            qdft_inv<16, 0, 1>(v);
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) st_soa(ring + piece(s, zr + cc, q), v[cc]);
+        }
+        if (more) issue(i + 1, 2, 3);
+        __syncthreads();
+
+        // ---- B': mirror of B
+        {
+            const int t = threadIdx.x;
+            const int q = t & 7, c = (t >> 3) & 15, k0 = t >> 7;
+            Q v[16];
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const int zz = 256 * k0 + 16 * k1 + c;
+                Q w = ld_soa(ring + piece(sl(zz / CHZ), zz, q));
+                qlift_b(w, wz[c * (k0 + 4 * k1)]);
+                v[brev(k1, 16)] = w;
+            }
+            qdft_inv<16, 0, 1>(v);
+#pragma unroll
+            for (int bb = 0; bb < 16; ++bb) {
+                const int zz = 256 * k0 + 16 * bb + c;
+                st_soa(ring + piece(sl(zz / CHZ), zz, q), v[bb]);
+            }
+        }
+        if (more) issue(i + 1, 3, 4);
+        cp_async_commit();
+        __syncthreads();
+
+        // ---- A': read the task back (frees the tile's ring slots), mirror of A
+        //      without the kinetic rotation, streaming stores
+        {
+            const int t = phase_tid();
+            const int zl = t & 255, h = t >> 8;
+            Q v[4][4];                                 // [k0][k2y] as stored
+#pragma unroll
+            for (int k0 = 0; k0 < 4; ++k0) {
+                const int zz = 256 * k0 + zl;
+#pragma unroll
+                for (int k2 = 0; k2 < P; ++k2) v[k0][k2] = ld_soa(ring + piece(sl(zz / CHZ), zz, 2 * k2 + h));
+            }
+            Lift<T> cw[P];
+#pragma unroll
+            for (int r = 1; r < P; ++r) cw[r] = tb[C + r - 1];
+            Lift<T> tw64[3];
+#pragma unroll
+            for (int k0 = 1; k0 < 4; ++k0) tw64[k0 - 1] = wz[16 * (zl >> 4) * k0];
+            __syncthreads();                           // every slot of tile i is free
+            if (more) issue(i + 1, NCH / 2, NCH);
+            cp_async_commit();
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) {
+                Q col[4];
+#pragma unroll
+                for (int k0 = 0; k0 < 4; ++k0) {
+                    col[brev(k0, 4)] = v[k0][k2];
+                    if (k0 > 0) qlift_b(col[brev(k0, 4)], tw64[k0 - 1]);
+                }
+                qdft_inv<4, 0, 1>(col);                // col[a]
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa) v[aa][k2] = col[aa];
+            }
+#pragma unroll
+            for (int aa = 0; aa < 4; ++aa) {
+                Q row[4];
+#pragma unroll
+                for (int k2 = 0; k2 < P; ++k2) row[brev(k2, 4)] = v[aa][k2];
+                qdft_inv<4, 0, 1>(row);                // row[r]
+#pragma unroll
+                for (int r = 1; r < P; ++r) qlift_b(row[r], cw[r]);
+                const int zz = 256 * aa + zl;
+                float2 *p = a.dst + colbase + (long long)zz * g.plane + 2 * h;
+#pragma unroll
+                for (int r = 0; r < P; ++r)
+                    __stcs(reinterpret_cast<float4 *>(p + ((long long)r << g.lgnx)),
+                           make_float4(row[r].x.x, row[r].y.x, row[r].x.y, row[r].y.y));
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
+// ============================================================== XY (packed)
+// Steady real-time XY pass (nx = 256, 64-row tiles, product potential,
+// merged half-kicks, in place), persistent with the ring of three 32-row
+// half buffers of xy_ring_kernel.  Stages as there: P1 inverse x last stage,
+// P2 inverse x first stage, P3a inverse y last stage, P3b inverse y first
+// stage + potential factor + forward y first stage, P3c forward y last
+// stage, P4 forward x first stage, P5 forward x last stage to HBM.
+//
+// Pairs: the x stages pair tile rows rw and rw + 32 (one in each half
+// buffer); between P1 and P2 and between P3c and P5 the tile is kept "split":
+// the real-part pair of a position in the first half buffer, the
+// imaginary-part pair in the second.  The y stages pair adjacent columns:
+// from P2 to P3c every 16-byte piece of a row holds (re_p, re_p+1, im_p,
+// im_p+1).  512 threads, 32 complex values (16 pairs) each per phase.
+namespace {
+
+// potential factor exp(-i th) as lifting pairs for |th| <= 0.16 (TIER 2:
+// series through the fifth order) or |th| <= 0.5 (TIER 1: through th^11 for
+// p and th^9 for u), own odd Taylor series of tan(th/2) and -sin(th)
+template <int TIER> __device__ __forceinline__ void qkick_coef(float2 th, float2 &p, float2 &u)
+{
+    const float2 t2 = mul2(th, th);
+    if constexpr (TIER == 2) {
+        // u = -sin th = th (-1 + t2/6 - t2^2/120), p = tan(th/2) = th (1/2 + t2/24 + t2^2/240)
+        u = mul2(th, fma2(t2, fma2(t2, pk(-1.0f / 120.0f), pk(1.0f / 6.0f)), pk(-1.0f)));
+        p = mul2(th, fma2(t2, fma2(t2, pk(1.0f / 240.0f), pk(1.0f / 24.0f)), pk(0.5f)));
+    } else {
+        float2 su = fma2(t2, pk(-1.0f / 362880.0f), pk(1.0f / 5040.0f));
+        su = fma2(t2, su, pk(-1.0f / 120.0f));
+        su = fma2(t2, su, pk(1.0f / 6.0f));
+        u = mul2(th, fma2(t2, su, pk(-1.0f)));
+        // tan(h), h = th/2: h + h^3/3 + 2h^5/15 + 17h^7/315 + 62h^9/2835 + 1382h^11/155925
+        float2 sp = fma2(t2, pk(1382.0f / 155925.0f / 2048.0f), pk(62.0f / 2835.0f / 512.0f));
+        sp = fma2(t2, sp, pk(17.0f / 315.0f / 128.0f));
+        sp = fma2(t2, sp, pk(2.0f / 15.0f / 32.0f));
+        sp = fma2(t2, sp, pk(1.0f / 3.0f / 8.0f));
+        p = mul2(th, fma2(t2, sp, pk(0.5f)));
+    }
+}
+
+constexpr int kXpkNT = 512;
+
+}  // namespace
+
+template <int TIER>
+__global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a, int ntiles)
+{
+    constexpr int NX = 256, RA = 16, RB = 16, LY = 64, YA = 8, YB = 8, NT = kXpkNT;
+    constexpr int PITCH = NX + 2;                // complex values per row (16-byte rows)
+    constexpr int HR = LY / 2;                   // rows per half buffer
+    constexpr int HB = HR * PITCH;               // complex values per half buffer
+    constexpr int PPR = NX / 2;                  // 16-byte pieces per row
+    constexpr int RPI = NT / PPR;                // rows per copy round
+    constexpr int NCR = HR / RPI;                // copy rounds per half (8)
+    static_assert(NCR == 8 && RA * RB == NX && YA * YB == LY, "geometry");
+    using T = float;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *bufs = reinterpret_cast<float2 *>(smraw);
+    Lift<T> *wx = reinterpret_cast<Lift<T> *>(bufs + 3 * HB);   // [rr RA + j] = exp(-2 pi i j rr/NX)
+    Lift<T> *wy = wx + NX;                                      // exp(-2 pi i e/LY)
+    __shared__ T gtab[2][LY];                    // g(y) of the tile's rows, per tile
+    __shared__ float2 htab[2][NX / 2];           // H(x, z) tau at swapped positions (pairs)
+    __shared__ T thzs[2];                        // z-only phase, per tile
+
+    const Geom &g = a.g;
+    const Kick<T> &k = a.k;
+    const int t0 = threadIdx.x;
+    const int G = gridDim.x;
+    const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
+    const T tau = k.tau_full;
+    auto unswx = [](int q) { return q / RA + RB * (q % RA); };
+    auto half_buf = [&](int i, int h) { return bufs + ((2 * i + h) % 3) * HB; };
+    const int cpiece = t0 % PPR, crow = t0 / PPR;
+    auto issue = [&](int i, int h, int m0, int m1) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        const float2 *src = a.src + (long long)z * g.plane +
+                            ((long long)((h * HR + crow + RPI * m0) * g.P + r) << g.lgnx) + 2 * cpiece;
+        float2 *dst = half_buf(i, h) + (crow + RPI * m0) * PITCH + 2 * cpiece;
+        const long long rstep = (long long)(RPI * g.P) << g.lgnx;
+        for (int m = m0; m < m1; ++m) {
+            cp_async16(dst, src);
+            src += rstep;
+            dst += RPI * PITCH;
+        }
+    };
+    auto load_tabs = [&](int i) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        if (t0 < LY) gtab[i & 1][t0] = k.g[r + t0 * g.P];
+        if (t0 < NX / 2) {
+            const long long hz = (long long)z * g.nx;
+            htab[i & 1][t0] = make_float2(k.H[hz + unswx(2 * t0)] * tau, k.H[hz + unswx(2 * t0 + 1)] * tau);
+        }
+        if (t0 == 0) thzs[i & 1] = k.vz ? k.vz[z & (g.nz - 1)] * tau : T(0);
+    };
+
+    if (nmine > 0) {
+        issue(0, 0, 0, NCR);
+        issue(0, 1, 0, NCR);
+        load_tabs(0);
+    }
+    cp_async_commit();
+    for (int e = t0; e < NX + LY; e += NT)
+        wx[e] = e < NX ? a.tw[g.fast_x_off + (e % RA) * (e / RA)] : a.tw[g.fast_y_off + e - NX];
+
+    for (int i = 0; i < nmine; ++i) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        const bool more = i + 1 < nmine;
+        if (more) load_tabs(i + 1);
+        cp_async_wait_all();
+        __syncthreads();                         // tile i (and its tables) visible
+        float2 *const b0 = half_buf(i, 0);
+        float2 *const b1 = half_buf(i, 1);
+
+        // P1: inverse x, last stage (radix RB), rows rw and rw + 32 as a pair;
+        //     AoS in, split out
+        {
+            const int t = threadIdx.x;
+            const int j = t & 15, rw = t >> 4;
+            float2 *pa = b0 + rw * PITCH, *pb = b1 + rw * PITCH;
+            Q v[RB];
+#pragma unroll
+            for (int kk = 0; kk < RB; ++kk) {
+                const float2 ea = pa[j + RA * kk], eb = pb[j + RA * kk];
+                v[brev(kk, RB)] = Q{make_float2(ea.x, eb.x), make_float2(ea.y, eb.y)};
+            }
+            qdft_inv<RB, 0, 1>(v);
+#pragma unroll
+            for (int rr = 1; rr < RB; ++rr) qlift_b(v[rr], wx[rr * RA + j]);
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) {
+                pa[j + RA * rr] = v[rr].x;
+                pb[j + RA * rr] = v[rr].y;
+            }
+        }
+        if (more) issue(i + 1, 0, 0, 2);
+        __syncthreads();
+
+        // P2: inverse x, first stage (radix RA) on 16 contiguous positions;
+        //     split in, column pairs out
+        {
+            const int t = threadIdx.x;
+            const int rw = t & 31, j = t >> 5;
+            float2 *pa = b0 + rw * PITCH + RA * j, *pb = b1 + rw * PITCH + RA * j;
+            Q v[RA];
+#pragma unroll
+            for (int m = 0; m < RA; m += 2) {
+                const float4 xr = *reinterpret_cast<const float4 *>(pa + m);
+                const float4 xi = *reinterpret_cast<const float4 *>(pb + m);
+                v[brev(m, RA)] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
+                v[brev(m + 1, RA)] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
+            }
+            qdft_inv<RA, 0, 1>(v);
+#pragma unroll
+            for (int m = 0; m < RA; m += 2) {
+                *reinterpret_cast<float4 *>(pa + m) = make_float4(v[m].x.x, v[m + 1].x.x, v[m].y.x, v[m + 1].y.x);
+                *reinterpret_cast<float4 *>(pb + m) = make_float4(v[m].x.y, v[m + 1].x.y, v[m].y.y, v[m + 1].y.y);
+            }
+        }
+        if (more) issue(i + 1, 0, 2, 4);
+        __syncthreads();
+
+        // row ii + YA kk (kk < YB) of the tile, at column piece q (16 bytes)
+        auto yrow = [&](int row, int q) { return (row < HR ? b0 : b1) + (row % HR) * PITCH + 2 * q; };
+
+        // P3a: inverse y, last stage (radix YB) on rows ii + YA kk, two
+        //      column pairs (pieces pp and pp + 64)
+        {
+            const int t = threadIdx.x;
+            const int pp = t & 63, ii = t >> 6;
+            Q v[2][YB];
+#pragma unroll
+            for (int kk = 0; kk < YB; ++kk) {
+                v[0][brev(kk, YB)] = ld_soa(yrow(ii + YA * kk, pp));
+                v[1][brev(kk, YB)] = ld_soa(yrow(ii + YA * kk, pp + 64));
+            }
+            qdft_inv<YB, 0, 1>(v[0]);
+            qdft_inv<YB, 0, 1>(v[1]);
+#pragma unroll
+            for (int rr = 1; rr < YB; ++rr) {
+                const Lift<T> tw = wy[ii * rr];
+                qlift_b(v[0][rr], tw);
+                qlift_b(v[1][rr], tw);
+            }
+#pragma unroll
+            for (int rr = 0; rr < YB; ++rr) {
+                st_soa(yrow(ii + YA * rr, pp), v[0][rr]);
+                st_soa(yrow(ii + YA * rr, pp + 64), v[1][rr]);
+            }
+        }
+        if (more) issue(i + 1, 0, 4, 6);
+        __syncthreads();
+
+        // P3b: inverse y first stage -> potential factor -> forward y first
+        //      stage on rows YA ii + kk (one half buffer)
+        {
+            const int t = threadIdx.x;
+            const int pp = t & 63, ii = t >> 6;
+            const T *gt = gtab[i & 1];
+            const T thz = thzs[i & 1];
+            Q v[2][YA];
+#pragma unroll
+            for (int kk = 0; kk < YA; ++kk) {
+                v[0][brev(kk, YA)] = ld_soa(yrow(YA * ii + kk, pp));
+                v[1][brev(kk, YA)] = ld_soa(yrow(YA * ii + kk, pp + 64));
+            }
+            qdft_inv<YA, 0, 1>(v[0]);
+            qdft_inv<YA, 0, 1>(v[1]);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float2 hx = htab[i & 1][pp + 64 * c];
+#pragma unroll
+                for (int rr = 0; rr < YA; ++rr) {
+                    // v[c][rr]: real-space row jy = ii + YB rr
+                    float2 p, u;
+                    qkick_coef<TIER>(fma2(pk(gt[ii + YB * rr]), hx, pk(thz)), p, u);
+                    qrot_f(v[c][rr], p, u);
+                }
+            }
+            qdft_fwd<YA, 0, 1>(v[0]);
+            qdft_fwd<YA, 0, 1>(v[1]);
+#pragma unroll
+            for (int kk = 0; kk < YA; ++kk) {
+                st_soa(yrow(YA * ii + kk, pp), v[0][brev(kk, YA)]);
+                st_soa(yrow(YA * ii + kk, pp + 64), v[1][brev(kk, YA)]);
+            }
+        }
+        if (more) issue(i + 1, 0, 6, 8);
+        cp_async_commit();
+        __syncthreads();
+
+        // P3c: forward y, last stage (radix YB) on rows ii + YA rr; column
+        //      pairs in, split out (rows ii + YA m and ii + YA m + 32 pair up)
+        {
+            const int t = phase_tid();
+            const int pp = t & 63, ii = t >> 6;
+            Q v[2][YB];
+#pragma unroll
+            for (int rr = 0; rr < YB; ++rr) {
+                v[0][rr] = ld_soa(yrow(ii + YA * rr, pp));
+                v[1][rr] = ld_soa(yrow(ii + YA * rr, pp + 64));
+            }
+#pragma unroll
+            for (int rr = 1; rr < YB; ++rr) {
+                const Lift<T> tw = wy[ii * rr];
+                qlift_f(v[0][rr], tw);
+                qlift_f(v[1][rr], tw);
+            }
+            qdft_fwd<YB, 0, 1>(v[0]);
+            qdft_fwd<YB, 0, 1>(v[1]);
+            // output row ii + YA k2 sits in v[c][brev(k2)]; rows k2 and k2 + 4
+            // (local row ii + YA m of each half buffer) form a pair
+#pragma unroll
+            for (int mm = 0; mm < YB / 2; ++mm) {
+                const int lr = ii + YA * mm;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const Q &qa = v[c][brev(mm, YB)], &qb = v[c][brev(mm + YB / 2, YB)];
+                    const int off = lr * PITCH + 2 * (pp + 64 * c);
+                    *reinterpret_cast<float4 *>(b0 + off) = make_float4(qa.x.x, qb.x.x, qa.x.y, qb.x.y);
+                    *reinterpret_cast<float4 *>(b1 + off) = make_float4(qa.y.x, qb.y.x, qa.y.y, qb.y.y);
+                }
+            }
+        }
+        __syncthreads();
+
+        // P4: forward x, first stage (radix RA) on 16 contiguous positions, split
+        {
+            const int t = threadIdx.x;
+            const int rw = t & 31, j = t >> 5;
+            float2 *pa = b0 + rw * PITCH + RA * j, *pb = b1 + rw * PITCH + RA * j;
+            Q v[RA];
+#pragma unroll
+            for (int m = 0; m < RA; m += 2) {
+                const float4 xr = *reinterpret_cast<const float4 *>(pa + m);
+                const float4 xi = *reinterpret_cast<const float4 *>(pb + m);
+                v[m] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
+                v[m + 1] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
+            }
+            qdft_fwd<RA, 0, 1>(v);
+#pragma unroll
+            for (int m = 0; m < RA; m += 2) {
+                const Q &e0 = v[brev(m, RA)], &e1 = v[brev(m + 1, RA)];
+                *reinterpret_cast<float4 *>(pa + m) = make_float4(e0.x.x, e0.x.y, e1.x.x, e1.x.y);
+                *reinterpret_cast<float4 *>(pb + m) = make_float4(e0.y.x, e0.y.y, e1.y.x, e1.y.y);
+            }
+        }
+        __syncthreads();
+
+        // P5: forward x, last stage, to HBM.  The task is read back first so
+        //     that both half buffers can take the next tile's second half.
+        {
+            const int t = threadIdx.x;
+            const int j = t & 15, rw = t >> 4;
+            Q v[RB];
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr)
+                v[rr] = Q{b0[rw * PITCH + j + RA * rr], b1[rw * PITCH + j + RA * rr]};
+            __syncthreads();                     // tile i's buffers are free
+            if (more) issue(i + 1, 1, 0, NCR);
+            cp_async_commit();
+#pragma unroll
+            for (int rr = 1; rr < RB; ++rr) qlift_f(v[rr], wx[rr * RA + j]);
+            qdft_fwd<RB, 0, 1>(v);
+            float2 *oa = a.dst + (long long)z * g.plane + ((long long)(rw * g.P + r) << g.lgnx) + j;
+            float2 *ob = oa + ((long long)(HR * g.P) << g.lgnx);
+#pragma unroll
+            for (int k2 = 0; k2 < RB; ++k2) {
+                const Q &e = v[brev(k2, RB)];
+                oa[RA * k2] = make_float2(e.x.x, e.y.x);
+                ob[RA * k2] = make_float2(e.x.y, e.y.y);
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
+// ================================================================ dispatch
+namespace {
+int pk_sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+}  // namespace
+
+bool packed_xy_supported(const Geom &g)
+{
+    return g.nx == 256 && g.Ly == 64;
+}
+
+bool launch_xy_packed(const XYArgs<float> &a, cudaStream_t st)
+{
+    const bool hot = a.flags == (XY_IN_MIXED | XY_OUT_MIXED | XY_KICK_FULL) &&
+                     a.k.form == VF_PRODUCT && !a.k.imag && a.small_angle >= 1;
+    if (!hot || !a.ring || a.src != a.dst || !packed_xy_supported(a.g)) return false;
+    constexpr int HB = 32 * 258;
+    constexpr size_t smem = 3 * HB * sizeof(float2) + (256 + 64) * sizeof(Lift<float>);
+    static bool cfg = false;
+    if (!cfg) {
+        cudaFuncSetAttribute(xy_pk_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(xy_pk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cfg = true;
+    }
+    const int ntiles = xy_grid(a.g);
+    const int grid = std::min(ntiles, pk_sm_count());
+    if (a.small_angle == 2)
+        xy_pk_kernel<2><<<grid, kXpkNT, smem, st>>>(a, ntiles);
+    else
+        xy_pk_kernel<1><<<grid, kXpkNT, smem, st>>>(a, ntiles);
+    return true;
+}
+
+bool packed_z_supported(const Geom &g)
+{
+    return g.nz == 1024 && g.P == 4 && g.w == 4;
+}
+
+bool launch_z_packed(const ZArgs<float> &a, cudaStream_t st)
+{
+    if (!a.ring || a.observe || a.imag || a.scale || a.src != a.dst || !a.kin_xy ||
+        !packed_z_supported(a.g))
+        return false;
+    constexpr size_t smem = (size_t)kZpkNRING * kZpkCHZ * 16 * sizeof(float2) +
+                            2 * 1024 * sizeof(Lift<float>);
+    static bool cfg = false;
+    if (!cfg) {
+        cudaFuncSetAttribute(z_pk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cfg = true;
+    }
+    const int ntiles = z_grid(a.g);
+    z_pk_kernel<<<std::min(ntiles, pk_sm_count()), kZpkNT, smem, st>>>(a, ntiles);
+    return true;
+}
+
+}  // namespace ctap

@@ -23,6 +23,7 @@ struct TabSet {
     void *kin;
     void *sep;
     bool sep_valid;
+    void *kin_xy = nullptr;        // complex64 real time: (kx, ky) rotations [ny][nx] (packed Z pass)
 };
 
 // an instantiated CUDA graph of one ctap_step call
@@ -51,6 +52,7 @@ struct PlanState {
     int timeout_ms = 60000;
     bool force_generic = false;    // CTAP_FORCE_GENERIC=1 at plan creation
     bool no_ring = false;          // CTAP_NO_RING=1: one-tile-per-CTA Z pass only
+    bool no_packed = false;        // CTAP_NO_PACKED=1: scalar persistent passes instead of packed
     bool fast_xy = false, fast_z = false;
     double vmax = 0.0;             // max |V| over the grid (small-angle kick test)
 
@@ -112,6 +114,8 @@ struct PlanState {
 void build_geometry(PlanState &p, int emax, int maxv);   // throws std::runtime_error
 void build_twiddles(PlanState &p, std::vector<unsigned char> &host, int maxv);
 void build_kinetic(const PlanState &p, double dt, int imag, std::vector<unsigned char> &host);
+// real time, complex64: Lift<float> of exp(-i (kx^2 + ky^2) dt/2), [ny][nx]
+void build_kinetic_xy(const PlanState &p, double dt, std::vector<unsigned char> &host);
 void build_k2h(const PlanState &p, std::vector<double> &host);
 void build_separable(const PlanState &p, double dt, int imag, std::vector<unsigned char> &host);
 void natural_spline_basis(const std::vector<double> &knots, const std::vector<double> &z,

@@ -359,53 +359,64 @@ def test_fast_and_generic_passes_match_oracle(ctap, shape, monkeypatch):
 
 
 def test_persistent_z_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
-    """The persistent Z pass (shared-memory ring refilled by asynchronous
-    copies while the previous tile is transformed) is used for 1024-point
-    z-lines with 4 row classes; it must agree with the one-tile-per-CTA Z pass
-    and with the oracle."""
+    """The persistent Z passes (shared-memory ring refilled by asynchronous
+    copies while the previous tile is transformed) run 1024-point z-lines
+    with 4 row classes: the packed form (FP32-pair arithmetic, two columns
+    per thread) by default, the scalar ring with CTAP_NO_PACKED=1 and the
+    one-tile-per-CTA pass with CTAP_NO_RING=1.  All three must agree with
+    each other and with the oracle."""
     shape, box = (1024, 256, 64), wl.CTAP_BOX
     psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=15) \
         * np.exp(2j * wl.mesh(shape, box)[2])
-    plan, V, c = guides_plan(ctap, shape, box, "c64")
-    info = plan.info()
-    assert info["fast_mask"] == 7 and info["row_classes"] == 4 and info["cols_per_z_tile"] == 16
-    psi = to_dev(psi0, "c64")
-    plan.step(psi, 2, 0.0025)
-    ring = psi.cpu().numpy().astype(complex)
-    monkeypatch.setenv("CTAP_NO_RING", "1")
-    pplan, _, _ = guides_plan(ctap, shape, box, "c64")
-    assert pplan.info()["fast_mask"] == 3
-    psi = to_dev(psi0, "c64")
-    pplan.step(psi, 2, 0.0025)
-    plain = psi.cpu().numpy().astype(complex)
-    assert rel(ring, plain) < 1e-6
-    ref = oracle.step(psi0, V, box, 0.0025, 2)
-    assert rel(ring, ref) < 1e-6
+    ref = oracle.step(psi0, *guides_plan(ctap, shape, box, "c128")[1:2], box, 0.0025, 2)
+    got = {}
+    for env, mask in ((None, 23), ("CTAP_NO_PACKED", 7), ("CTAP_NO_RING", 3)):
+        if env:
+            monkeypatch.setenv(env, "1")
+        plan, V, c = guides_plan(ctap, shape, box, "c64")
+        info = plan.info()
+        assert info["fast_mask"] == mask and info["row_classes"] == 4 and \
+            info["cols_per_z_tile"] == 16, info
+        psi = to_dev(psi0, "c64")
+        plan.step(psi, 2, 0.0025)
+        got[env] = psi.cpu().numpy().astype(complex)
+        plan.close()
+        if env:
+            monkeypatch.delenv(env)
+    assert rel(got[None], got["CTAP_NO_PACKED"]) < 1e-6
+    assert rel(got["CTAP_NO_PACKED"], got["CTAP_NO_RING"]) < 1e-6
+    for v in got.values():
+        assert rel(v, ref) < 1e-6
 
 
 def test_persistent_xy_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
-    """The persistent XY pass (three 32-row half buffers, the next tile copied
-    in while the current one is transformed) runs the steady steps of
-    256-wide complex64 planes with 64-row tiles; 1024 tiles over at most 148
-    CTAs exercise the prefetch.  It must agree with the one-tile-per-CTA XY
-    pass and with the oracle."""
+    """The persistent XY passes (three 32-row half buffers, the next tile
+    copied in while the current one is transformed) run the steady steps of
+    256-wide complex64 planes with 64-row tiles: in packed FP32-pair
+    arithmetic by default, in scalar arithmetic with CTAP_NO_PACKED=1, and
+    one tile per CTA with CTAP_NO_RING=1.  1024 tiles over at most 148 CTAs
+    exercise the prefetch.  All three must agree with each other and with
+    the oracle."""
     shape, box = (256, 256, 256), wl.CTAP_BOX
     psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=17) \
         * np.exp(2j * wl.mesh(shape, box)[2])
-    plan, V, c = guides_plan(ctap, shape, box, "c64")
-    assert plan.info()["fast_mask"] & 9 == 9
-    psi = to_dev(psi0, "c64")
-    plan.step(psi, 4, 0.0025)
-    ring = psi.cpu().numpy().astype(complex)
-    monkeypatch.setenv("CTAP_NO_RING", "1")
-    pplan, _, _ = guides_plan(ctap, shape, box, "c64")
-    assert pplan.info()["fast_mask"] & 9 == 1
-    psi = to_dev(psi0, "c64")
-    pplan.step(psi, 4, 0.0025)
-    plain = psi.cpu().numpy().astype(complex)
-    assert rel(ring, plain) < 1e-6
+    got = {}
+    for env, bits in ((None, 41), ("CTAP_NO_PACKED", 9), ("CTAP_NO_RING", 1)):
+        if env:
+            monkeypatch.setenv(env, "1")
+        plan, V, c = guides_plan(ctap, shape, box, "c64")
+        assert plan.info()["fast_mask"] & 41 == bits, plan.info()
+        psi = to_dev(psi0, "c64")
+        plan.step(psi, 4, 0.0025)
+        got[env] = psi.cpu().numpy().astype(complex)
+        plan.close()
+        if env:
+            monkeypatch.delenv(env)
     ref = oracle.step(psi0, V, box, 0.0025, 4)
-    assert rel(ring, ref) < 1e-6
+    assert rel(got[None], got["CTAP_NO_PACKED"]) < 1e-6
+    assert rel(got["CTAP_NO_PACKED"], got["CTAP_NO_RING"]) < 1e-6
+    for v in got.values():
+        assert rel(v, ref) < 1e-6
 
 
 def test_ring_with_16_byte_aligned_psi(ctap):
