@@ -36,7 +36,14 @@ SHAPE = (1024, 256, 256)
 DT = 0.0025
 SPLIT = 50                 # split steps per bench step (one observation interval)
 SPLIT_FP64 = 4
-FP64_PEAK_TFLOPS = 1.25    # nominal B300 FP64 rate (no measured figure on this machine)
+FP64_NOMINAL_TFLOPS = 1.25  # nominal B300 FP64 rate (used only if the probe fails)
+ACC_STEPS = 500            # split steps of the complex64-vs-complex128 accuracy run
+# size x precision sweep: (nz, ny, nx); the paper's 256x64x1024 grid last
+SWEEP_SHAPES = [(64, 64, 64), (128, 128, 128), (256, 256, 256), (512, 256, 256),
+                (1024, 256, 256), (1024, 64, 256)]
+SWEEP_STEPS = 500          # split steps of each complex64-vs-complex128 comparison
+SWEEP_DT = 0.005
+L2_BYTES = 126 * 2 ** 20
 
 
 def pass_flops_per_point(shape, P):
@@ -49,7 +56,8 @@ def pass_flops_per_point(shape, P):
     xy = 2 * 5 * (math.log2(nx) + math.log2(ny // P)) + 6
     z = 2 * 5 * (math.log2(P) + math.log2(nz)) + 6
     return xy, z
-KERNEL_SOURCES = ["device_fft.cuh", "kernels.cuh", "kernels.cu", "fast_passes.cu"]
+KERNEL_SOURCES = ["device_fft.cuh", "kernels.cuh", "kernels.cu", "fast_passes.cu",
+                  "packed_passes.cu"]
 
 
 def args_():
@@ -60,6 +68,7 @@ def args_():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--no-sweep", action="store_true")
     return p.parse_args()
 
 
@@ -457,17 +466,125 @@ def time_rows(ctap, wl, torch, device, stream):
     return out
 
 
-def cpu_baseline(seconds_cap=30.0):
-    """The FP64 oracle, as it stands, on the host cores: split steps of the
-    full 256x256x1024 workload, as many as fit in about `seconds_cap`."""
+def rel_l2(torch, a, b):
+    """||a - b|| / ||b|| on the device, in FP64."""
+    a = a.to(torch.complex128)
+    b = b.to(torch.complex128)
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def norm_dv(torch, psi, dV):
+    return float(torch.sum(psi.to(torch.complex128).abs() ** 2)) * dV
+
+
+def accuracy_c64_vs_c128(ctap, wl, torch, device, stream, steps=ACC_STEPS):
+    """The accuracy the complex64 speed is quoted at: complex64 and
+    complex128 runs of the bench workload from the same psi0 for the same
+    number of split steps; relative L2 of the complex64 state against the
+    complex128 one and the norm drift of each."""
+    out = {"steps": steps, "dt": DT}
+    states = {}
+    for dtype, t in (("c64", torch.complex64), ("c128", torch.complex128)):
+        plan = build_plan(ctap, wl, dtype, stream)
+        psi = initial_state(wl, t, torch, device)
+        n0 = plan.observables(psi)[0]
+        with torch.cuda.stream(stream):
+            plan.step(psi, steps, DT)
+        obs = plan.observables(psi)
+        out[f"norm_drift_{dtype}"] = float(obs[0] / n0 - 1.0)
+        out[f"populations_{dtype}"] = [float(x) for x in obs[3:]]
+        states[dtype] = psi
+        plan.close()
+    out["rel_l2_c64_vs_c128"] = rel_l2(torch, states["c64"], states["c128"])
+    del states
+    torch.cuda.empty_cache()
+    return out
+
+
+def sweep_case(wl, shape, potential):
+    """Box, potential setter and psi0 of one sweep point: the harmonic
+    oscillator on [-8,8]^3 or the three guides on the guide box; psi0 a
+    normalised sum of 4 Gaussians, centres U[-4,4]^3, widths U[0.8,2],
+    numpy.random.default_rng(0)."""
+    if potential == "harmonic":
+        box = wl.HARMONIC_BOX
+
+        def setup(plan):
+            plan.set_potential_separable(*wl.harmonic_parts(shape, box))
+    else:
+        box = wl.CTAP_BOX
+        c = wl.guide_centres(wl.axis(shape[0], box[4], box[5]))
+
+        def setup(plan):
+            plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    return box, setup, wl.gaussian_sum(shape, box, seed=0)
+
+
+def time_sweep(ctap, wl, torch, device, stream, hbm, steps=SWEEP_STEPS):
+    """Size x precision sweep (harmonic and guide potentials, complex64 and
+    complex128): split steps per second (CUDA events, graph replay), design
+    HBM bytes per second (32 B per point and step for complex64, 64 B for
+    complex128) and its fraction of the measured copy bandwidth where psi
+    does not fit in L2, and the relative L2 of complex64 against complex128
+    after `steps` steps from the same psi0."""
+    rows = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for shape in SWEEP_SHAPES:
+        npts = int(np.prod(shape))
+        for potential in ("ctap", "harmonic"):
+            box, setup, psi0 = sweep_case(wl, shape, potential)
+            row = {"grid": list(shape[::-1]), "potential": potential, "steps": steps,
+                   "dt": SWEEP_DT}
+            finals = {}
+            for dtype, t, esize in (("c64", torch.complex64, 8), ("c128", torch.complex128, 16)):
+                plan = ctap.Plan(shape, box, dtype, stream=stream)
+                setup(plan)
+                psi = torch.from_numpy(psi0).to(device, t)
+                n0 = plan.observables(psi)[0]
+                with torch.cuda.stream(stream):
+                    plan.step(psi, steps, SWEEP_DT)     # the accuracy run
+                n1 = plan.observables(psi)[0]           # synchronises the plan stream
+                finals[dtype] = psi.clone()
+                nt = 100 if dtype == "c64" else 20
+                with torch.cuda.stream(stream):
+                    plan.step(psi, nt, SWEEP_DT)
+                    plan.step(psi, nt, SWEEP_DT)        # graph captured here
+                    e0.record(stream)
+                    plan.step(psi, nt, SWEEP_DT)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / nt
+                gbps = 4 * npts * esize / (ms * 1e-3) / 1e9
+                row[dtype] = {"steps_per_s": 1000.0 / ms, "ms_per_step": ms,
+                              "point_updates_per_s": npts * 1000.0 / ms, "design_GBps": gbps,
+                              "hbm_frac": gbps / hbm if npts * esize > L2_BYTES else None,
+                              "norm_drift": float(n1 / n0 - 1.0),
+                              "fast_mask": plan.info()["fast_mask"]}
+                plan.close()
+                del psi
+            row["rel_l2_c64_vs_c128"] = rel_l2(torch, finals["c64"], finals["c128"])
+            row["fp32_speedup"] = row["c64"]["steps_per_s"] / row["c128"]["steps_per_s"]
+            rows.append(row)
+            del finals
+            torch.cuda.empty_cache()
+    return rows
+
+
+
+def cpu_baseline_leg(ctap, wl, torch, device, stream, seconds_cap=30.0, sweep=True):
+    """The FP64 oracle, as it stands, on the host cores.  Timed: split steps
+    of the full 256x256x1024 workload, as many as fit in about
+    `seconds_cap`.  The oracle's own results then anchor the GPU paths: the
+    relative L2 of the complex64 and complex128 states after the same steps
+    from the same psi0, and after 2 steps at every sweep point."""
     import oracle
-    from paper_1309_2451_b300 import workloads as wl
     box = wl.CTAP_BOX
     z = wl.axis(SHAPE[0], box[4], box[5])
     c = wl.guide_centres(z)
     V = oracle.ctap_potential(SHAPE, box, wl.V0, wl.SIGMA_GUIDE, c[0], c[2])
     xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
-    psi = wl.packet_from_transverse(wl.guide_seed_2d(SHAPE[1:], box, xc), SHAPE[0], box)
+    psi0 = wl.packet_from_transverse(wl.guide_seed_2d(SHAPE[1:], box, xc), SHAPE[0], box)
+    psi = psi0
     n, t_total = 0, 0.0
     while t_total < seconds_cap and n < 10:
         t0 = time.perf_counter()
@@ -476,10 +593,51 @@ def cpu_baseline(seconds_cap=30.0):
         n += 1
         if n == 1 and t_total > seconds_cap / 2:
             break
-    return {"value": n / t_total, "unit": "steps/s", "cores": oracle.num_threads(),
+    base = {"value": n / t_total, "unit": "steps/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{n} FP64 split step(s) of the 256x256x1024 three-guide workload "
                       f"({t_total:.1f} s, OpenMP over lines)"}
+    ref = torch.from_numpy(psi).to(device)
+    del psi, V
+    parity = {"steps": n, "workload": "ctap_large, the bench psi0"}
+    for dtype, t in (("c64", torch.complex64), ("c128", torch.complex128)):
+        plan = build_plan(ctap, wl, dtype, stream)
+        g = torch.from_numpy(psi0).to(device, t)
+        with torch.cuda.stream(stream):
+            plan.step(g, n, DT)
+        torch.cuda.synchronize()
+        parity[dtype] = rel_l2(torch, g, ref)
+        plan.close()
+        del g
+    del ref
+    torch.cuda.empty_cache()
+    sweep_parity = []
+    if sweep:
+        for shape in SWEEP_SHAPES:
+            for potential in ("ctap", "harmonic"):
+                sbox, setup, p0 = sweep_case(wl, shape, potential)
+                if potential == "harmonic":
+                    Vs = wl.harmonic_dense(shape, sbox)
+                else:
+                    cz = wl.guide_centres(wl.axis(shape[0], sbox[4], sbox[5]))
+                    Vs = oracle.ctap_potential(shape, sbox, wl.V0, wl.SIGMA_GUIDE, cz[0], cz[2])
+                r = torch.from_numpy(oracle.step(p0, Vs, sbox, SWEEP_DT, 2)).to(device)
+                del Vs
+                row = {"grid": list(shape[::-1]), "potential": potential, "steps": 2}
+                for dtype, t in (("c64", torch.complex64), ("c128", torch.complex128)):
+                    plan = ctap.Plan(shape, sbox, dtype, stream=stream)
+                    setup(plan)
+                    g = torch.from_numpy(p0).to(device, t)
+                    with torch.cuda.stream(stream):
+                        plan.step(g, 2, SWEEP_DT)
+                    torch.cuda.synchronize()
+                    row[dtype] = rel_l2(torch, g, r)
+                    plan.close()
+                    del g
+                sweep_parity.append(row)
+                del r
+                torch.cuda.empty_cache()
+    return base, parity, sweep_parity
 
 
 def run_reference(a):
@@ -517,6 +675,19 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def dominant_pass(plan, counts, pms):
+    """(kind, kernel name, average ms) of the pass with the larger share."""
+    kind = 0 if pms[0] >= pms[1] else 1
+    fast = plan.info()["fast_mask"]
+    if kind == 0:
+        name = ("xy_pk_kernel" if fast & 32 else "xy_ring_kernel" if fast & 8 else
+                "xy_fast_kernel" if fast & 1 else "xy_pass_kernel")
+    else:
+        name = ("z_pk_kernel" if fast & 16 else "z_ring_kernel" if fast & 4 else
+                "z_fast_kernel" if fast & 2 else "z_pass_kernel")
+    return kind, name, pms[kind] / max(counts[kind], 1)
+
+
 def run_ours(a):
     import torch
     from paper_1309_2451_b300 import build, ctap, workloads as wl
@@ -530,67 +701,96 @@ def run_ours(a):
         dist.init_process_group("nccl", device_id=device)
     stream = torch.cuda.Stream(device=device)
     reduce = make_reduce(dist, torch, device)
+    barrier = dist.barrier if dist is not None else None
 
+    # the headline: profiling off, so repeated ctap_step calls replay a graph
     res = time_path(ctap, wl, torch, "c64", SPLIT, a.steps, a.warmup, device, stream,
-                    barrier=dist.barrier if dist is not None else None)
+                    profile=False, barrier=barrier)
+    # the per-pass breakdown of the same loop: per-launch CUDA events recorded
+    # by the library on its stream (graph replay off while they are on)
+    prof = time_path(ctap, wl, torch, "c64", SPLIT, min(a.steps, 5), 1, device, stream,
+                     profile=True, barrier=barrier)
 
     N = int(np.prod(SHAPE))
     esize = 8
     hbm, peak_kind = peaks()
-    counts, pms = res["counts"], res["pass_ms"]
-    kind = 0 if pms[0] >= pms[1] else 1
-    fast = res["plan"].info()["fast_mask"]
-    name = (("xy_ring_kernel" if fast & 8 else ("xy_fast_kernel" if fast & 1 else "xy_pass_kernel"))
-            if kind == 0
-            else ("z_ring_kernel" if fast & 4 else ("z_fast_kernel" if fast & 2 else "z_pass_kernel")))
-    avg_ms = pms[kind] / max(counts[kind], 1)
+    counts, pms = prof["counts"], prof["pass_ms"]
+    kind, name, avg_ms = dominant_pass(prof["plan"], counts, pms)
     bytes_launch = 2 * N * esize       # one read and one write of psi
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": recorded_traffic(name),
                 "kernel": name, "peak_kind": peak_kind,
                 "step_design_GBps": 4 * N * esize * a.steps * SPLIT / (res["ms"] * 1e-3) / 1e9}
+    passes = {"xy_ms_per_launch": pms[0] / max(counts[0], 1),
+              "z_ms_per_launch": pms[1] / max(counts[1], 1),
+              "launches": list(counts), "ms_total": [float(x) for x in pms],
+              "timed_bench_steps": min(a.steps, 5),
+              "note": "separate profiled run of the same loop (graph replay off)"}
+    prof["plan"].close()
+    del prof
 
     extra = {}
+    if rank == 0:
+        try:
+            extra["fma_peaks"] = dict(ctap.measure_fma_peaks(stream), unit="TFLOP/s",
+                                      how="CUDA events, FMA-bound probe kernels (ctap_measure_fma_peaks)")
+        except Exception as e:   # the probe is reported, never fatal
+            extra["fma_peaks"] = {"error": str(e)}
+    fp64_peak = extra.get("fma_peaks", {}).get("fp64_tflops")
     if rank == 0 and not a.no_fp64:
-        r64 = time_path(ctap, wl, torch, "c128", SPLIT_FP64, max(2, a.steps // 10), 1, device,
-                        stream)
-        ms64 = r64["ms"] / (max(2, a.steps // 10) * SPLIT_FP64)
-        c64, p64 = r64["counts"], r64["pass_ms"]
-        k64 = 0 if p64[0] >= p64[1] else 1
-        avg64 = p64[k64] / max(c64[k64], 1)
+        n64 = max(2, a.steps // 10)
+        r64 = time_path(ctap, wl, torch, "c128", SPLIT_FP64, n64, 1, device, stream,
+                        profile=False)
+        ms64 = r64["ms"] / (n64 * SPLIT_FP64)
+        r64["plan"].close()
+        p64 = time_path(ctap, wl, torch, "c128", SPLIT_FP64, 2, 1, device, stream, profile=True)
+        k64, name64, avg64 = dominant_pass(p64["plan"], p64["counts"], p64["pass_ms"])
         ach64 = 2 * N * 16 / (avg64 * 1e-3) / 1e9
-        P64 = r64["plan"].info()["row_classes"]
+        P64 = p64["plan"].info()["row_classes"]
         fxy, fz = pass_flops_per_point(SHAPE, P64)
         tflops = (fxy if k64 == 0 else fz) * N / (avg64 * 1e-3) / 1e12
-        fast64 = r64["plan"].info()["fast_mask"]
+        peak64 = fp64_peak if fp64_peak else FP64_NOMINAL_TFLOPS
         extra["fp64_path"] = {
             "steps_per_s": 1000.0 / ms64, "ms_per_step": ms64,
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                         "peak_kind": "nominal FP64 (profiling recipe)",
-                         "kernel": ("xy_" if k64 == 0 else "z_") + ("fast" if fast64 else "pass")
-                                   + "_kernel<double>",
-                         "flops_per_point": fxy if k64 == 0 else fz},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak64,
+                         "unit": "TFLOP/s", "frac": tflops / peak64,
+                         "peak_kind": "measured FP64 FMA rate (ctap_measure_fma_peaks)"
+                                      if fp64_peak else "nominal FP64 (profiling recipe)",
+                         "kernel": name64.replace("_kernel", "_kernel<double>"),
+                         "flops_per_point": fxy if k64 == 0 else fz,
+                         "flop_count": "radix-2 5 n log2 n per transform + 6 per factor"},
             "hbm_frac_of_dominant_kernel": ach64 / hbm,
             "fp32_speedup": (1000.0 / (res["ms"] / (a.steps * SPLIT))) / (1000.0 / ms64),
-            "dtype": "f64", "obs": [float(x) for x in r64["obs"]]}
-        del r64
+            "dtype": "f64", "obs": [float(x) for x in p64["obs"]]}
+        p64["plan"].close()
+        del r64, p64
+        extra["fp64_path"]["fp32_speedup_accuracy"] = accuracy_c64_vs_c128(ctap, wl, torch, device,
+                                                                            stream)
         rdf = time_path(ctap, wl, torch, "c128df", SPLIT_FP64, max(2, a.steps // 10), 1, device,
-                        stream)
+                        stream, profile=False)
         msdf = rdf["ms"] / (max(2, a.steps // 10) * SPLIT_FP64)
         extra["fp64_df_path"] = {
             "steps_per_s": 1000.0 / msdf, "ms_per_step": msdf,
             "arithmetic": "double-float (FP32 pairs, ~48-bit significands) on complex128 psi",
             "speedup_over_fp64": ms64 / msdf,
             "obs": [float(x) for x in rdf["obs"]]}
+        rdf["plan"].close()
         del rdf
     if rank == 0 and not a.no_extras:
         extra["rows"] = time_rows(ctap, wl, torch, device, stream)
         extra["variants"] = time_variants(torch, wl, device, stream, res["plan"], res["psi"])
         extra["variants"]["batched_sweep"] = time_batched(torch, wl, device, stream)
         extra["cufft_comparison"] = time_cufft(torch, device, stream, res["plan"])
-        extra["cpu_baseline"] = cpu_baseline()
+    if rank == 0 and not a.no_sweep:
+        extra["sweep"] = time_sweep(ctap, wl, torch, device, stream, hbm)
+    if rank == 0 and not a.no_extras:
+        base, parity, sweep_parity = cpu_baseline_leg(ctap, wl, torch, device, stream,
+                                                      sweep=not a.no_sweep)
+        extra["cpu_baseline"] = base
+        extra["rel_l2_vs_oracle"] = parity
+        if sweep_parity:
+            extra["sweep_rel_l2_vs_oracle"] = sweep_parity
     e2e = time_e2e(ctap, wl, torch, max(3, a.steps // 4), device, stream, res["plan"])
     ms, value, e2e["value"] = combine_ranks(res["ms"], e2e["value"], a.steps, world, reduce)
 
@@ -607,6 +807,7 @@ def run_ours(a):
                            "l2": "inputs larger than L2 (psi = 512 MiB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline,
+                "passes": passes,
                 "clocks": res["clocks"],
                 "gpu_launches": res["launches"] * world,
                 "e2e": e2e,

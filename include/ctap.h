@@ -266,6 +266,16 @@ ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);
 ctap_status ctap_norm_noalloc(const void *psi, long long n, ctap_dtype dtype, double dV,
                               void *cuda_stream, double *out);
 
+/* Arithmetic peaks of the current device, measured (not in the paper: the
+ * denominators of the arithmetic rooflines the bench reports).  Runs three
+ * FMA-bound probe kernels on cuda_stream (NULL = legacy default stream),
+ * each timed with CUDA events after a warm-up launch, and writes host
+ * out[0] = FP32 TFLOP/s with scalar FMA, out[1] = FP32 TFLOP/s with the
+ * packed FP32-pair FMA (fma.rn.f32x2), out[2] = FP64 TFLOP/s (an FMA counts
+ * two operations).  Synchronises; takes a few milliseconds.  Errors:
+ * CTAP_ERR_INVALID_ARG (null out), CTAP_ERR_CUDA. */
+ctap_status ctap_measure_fma_peaks(void *cuda_stream, double *out);
+
 const char *ctap_status_string(ctap_status s);
 const char *ctap_last_error(ctap_plan_t plan);   /* plan-local message; "" if none */
 const char *ctap_version(void);

@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
     if (t < LY) {
         const int y = r + t * g.P;
         if (HOT || k.form == VF_PRODUCT) gtab[t] = k.g[y];
-        else if (k.form == VF_SEPARABLE) ytab[t] = (full ? k.sep_full : k.sep_half)[g.nx + y];
+        // (the observables pass has no kick and no separable tables)
+        else if (k.form == VF_SEPARABLE && kick) ytab[t] = (full ? k.sep_full : k.sep_half)[g.nx + y];
     }
     if (t < NX && (HOT || k.form == VF_PRODUCT))
         htab[t] = k.H[(long long)z * g.nx + unswx(t)] * tau;

@@ -63,6 +63,7 @@ def lib():
         "ctap_pass_times": [_vp, ctypes.POINTER(ll), _dp],
         "ctap_plan_info": [_vp, ctypes.POINTER(ll)],
         "ctap_norm_noalloc": [_vp, ll, i, d, _vp, _vp],
+        "ctap_measure_fma_peaks": [_vp, _dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -86,7 +87,7 @@ def exported_symbols():
             "ctap_set_profiling", "ctap_pass_times", "ctap_plan_info", "ctap_status_string",
             "ctap_last_error", "ctap_version", "ctap_norm_noalloc", "ctap_add_potential_z",
             "ctap_density_xz", "ctap_plan_create_batched", "ctap_set_guides_batched",
-            "ctap_set_potential_wires"]
+            "ctap_set_potential_wires", "ctap_measure_fma_peaks"]
 
 
 def _f64(a, n=None):
@@ -311,6 +312,20 @@ def ctap_adjoint_apply(c12, c23, plan, psi0, nsteps, dt, K=32, guide=3, V0=20.0,
         _CtapAdjoint = _adjoint_function()
     return _CtapAdjoint.apply(c12, c23, plan, psi0, nsteps, dt, K, guide, V0, s, knots,
                               halfwidth)
+
+
+def measure_fma_peaks(stream=None):
+    """Measured FP32 (scalar FMA), FP32 (packed pair FMA) and FP64 TFLOP/s of
+    the current device (ctap_measure_fma_peaks)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = np.zeros(3)
+    rc = lib().ctap_measure_fma_peaks(_vp(stream.cuda_stream), _p(out))
+    if rc != 0:
+        raise CtapError(rc, "ctap_measure_fma_peaks")
+    return {"fp32_tflops": float(out[0]), "fp32x2_tflops": float(out[1]),
+            "fp64_tflops": float(out[2])}
 
 
 NOALLOC_MAX_ELEMENTS = 16384 * 8192

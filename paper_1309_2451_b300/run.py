@@ -6,8 +6,13 @@
 Grid sizes are given as nx ny nz.  The initial state is the guide-1 seed
 (optionally refined by --imag-prep imaginary-time steps on an nz = 1 plane,
 the transverse ground state of Sec. V) times a z-packet at z = -40 with
-momentum 2.  Every --every steps the FP64 observables (norm, <T>, <V>, guide
-populations) are printed as one JSON line.
+momentum --k0 (default 2).  --order intuitive exchanges the two separation
+profiles (Fig. 4b); --trap adds the longitudinal harmonic trap of Sec. III,
+which carries a packet released at rest at z = -40 through both coupling
+regions to z = +40 in half a trap period (the full transfer of Fig. 4:
+--k0 0 --trap --steps 15708 --dt 0.0025).  Every --every steps the FP64
+observables (norm, <T>, <V>, guide populations) are printed as one JSON
+line.
 """
 import argparse
 import json
@@ -24,6 +29,10 @@ def main(argv=None):
     p.add_argument("--every", type=int, default=50)
     p.add_argument("--dt", type=float, default=0.005)
     p.add_argument("--imag-prep", type=int, default=0)
+    p.add_argument("--order", choices=["counter", "intuitive"], default="counter")
+    p.add_argument("--trap", action="store_true",
+                   help="add the longitudinal trap omega^2 z^2/2 (Sec. III)")
+    p.add_argument("--k0", type=float, default=2.0, help="initial z-momentum of the packet")
     a = p.parse_args(argv)
 
     import torch
@@ -33,8 +42,8 @@ def main(argv=None):
     nx, ny, nz = a.grid
     box = wl.CTAP_BOX
     z = wl.axis(nz, box[4], box[5])
-    c = wl.guide_centres(z)
-    xc = float(wl.guide_centres(np.array([-40.0]))[0, 0])
+    c = wl.guide_centres(z, a.order)
+    xc = float(wl.guide_centres(np.array([-40.0]), a.order)[0, 0])
     phi = wl.guide_seed_2d((ny, nx), box, xc)
     tdt = torch.complex64 if a.dtype == "c64" else torch.complex128
     if a.imag_prep > 0:
@@ -47,9 +56,11 @@ def main(argv=None):
         prep.step(t, a.imag_prep, 0.01, imag=True)
         phi = t.cpu().numpy().astype(np.complex128)
         prep.close()
-    psi = torch.from_numpy(wl.packet_from_transverse(phi, nz, box)).to("cuda", tdt)
+    psi = torch.from_numpy(wl.packet_from_transverse(phi, nz, box, k0=a.k0)).to("cuda", tdt)
     plan = ctap.Plan((nz, ny, nx), box, a.dtype)
     plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    if a.trap:
+        plan.add_potential_z(wl.trap_z(z))
     done = 0
     t0 = time.perf_counter()
     while done < a.steps:

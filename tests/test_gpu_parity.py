@@ -213,6 +213,26 @@ def test_observables_separable_and_dense(ctap):
         assert np.all(got[3:] == 0.0)
 
 
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-6), ("c128", 1e-12)])
+@pytest.mark.parametrize("shape", [(64, 64, 64), (256, 64, 256)])
+def test_observables_separable_on_specialised_passes(ctap, shape, dtype, tol):
+    """Observables of the harmonic (separable) potential on grids that take
+    the specialised XY pass: the observe pass applies no kick and must not
+    touch the kick tables (which the observables call does not build)."""
+    box = (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
+    plan, V = harmonic_plan(ctap, shape, box, dtype)
+    assert plan.info()["fast_mask"] & 1, plan.info()
+    psi0 = wl.gaussian_sum(shape, box, seed=0)
+    psi = to_dev(psi0, dtype)
+    got = plan.observables(psi)
+    ref = oracle.observables(psi.cpu().numpy().astype(complex), V, box)
+    assert np.allclose(got[:3], ref[:3], rtol=tol, atol=tol * 1e-3), (got, ref)
+    plan.step(psi, 5, 0.005)
+    got = plan.observables(psi)
+    ref = oracle.observables(psi.cpu().numpy().astype(complex), V, box)
+    assert np.allclose(got[:3], ref[:3], rtol=tol, atol=tol * 1e-3), (got, ref)
+
+
 # ------------------------------------------------------------------ adjoint
 ADJ_SHAPE = (32, 16, 32)
 ADJ_BOX = (-9.0, 9.0, -6.0, 6.0, -24.0, 24.0)
