@@ -276,6 +276,16 @@ ctap_status ctap_norm_noalloc(const void *psi, long long n, ctap_dtype dtype, do
  * CTAP_ERR_INVALID_ARG (null out), CTAP_ERR_CUDA. */
 ctap_status ctap_measure_fma_peaks(void *cuda_stream, double *out);
 
+/* Record of the bounds-checked build (compiled with -DCTAP_DEBUG_BOUNDS;
+ * not in the paper).  That build compares every shared-memory and HBM index
+ * of the production passes with its buffer before the access; the first
+ * violation is recorded and the access skipped (nothing traps).  *out = 0:
+ * no violation since the last clear; > 0: check site << 48 | index of the
+ * first violation; -1: a normal build without checks.  clear != 0 resets
+ * the record.  Synchronises the device.  Errors: CTAP_ERR_INVALID_ARG (null
+ * out), CTAP_ERR_CUDA. */
+ctap_status ctap_debug_bounds(int clear, long long *out);
+
 const char *ctap_status_string(ctap_status s);
 const char *ctap_last_error(ctap_plan_t plan);   /* plan-local message; "" if none */
 const char *ctap_version(void);

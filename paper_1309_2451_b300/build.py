@@ -27,10 +27,15 @@ def _compile(src, obj, extra, verbose):
     return obj
 
 
-def build(force=False, verbose=False, extra=()):
+DEBUG_LIB = os.path.join(HERE, "libctap_debug.so")
+
+
+def build(force=False, verbose=False, extra=(), debug=False):
     """Compile the csrc/*.cu files whose objects are out of date in parallel
     (one nvcc per file; the largest file bounds the wall time), then link
-    libctap.so."""
+    libctap.so.  debug=True also links libctap_debug.so, the bounds-checked
+    build: the sources that include bounds.cuh recompiled with
+    -DCTAP_DEBUG_BOUNDS (objects under _build/debug), the others shared."""
     from concurrent.futures import ThreadPoolExecutor
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
@@ -59,14 +64,34 @@ def build(force=False, verbose=False, extra=()):
     if todo:
         with ThreadPoolExecutor(max_workers=len(todo)) as ex:
             list(ex.map(lambda so: _compile(so[0], so[1], extra, verbose), todo))
-    elif os.path.exists(LIB) and all(os.path.getmtime(o) <= os.path.getmtime(LIB) for o in objs):
-        return LIB
-    cmd = ["nvcc", *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
+    if todo or not os.path.exists(LIB) or \
+            any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
+        _link(LIB, objs, verbose)
+    if debug:
+        bounds = os.path.join(CSRC, "bounds.cuh")
+        ddir = os.path.join(objdir, "debug")
+        os.makedirs(ddir, exist_ok=True)
+        dobjs = []
+        for src, obj in zip(srcs, objs):
+            if bounds in deps(src, set()):
+                dobj = os.path.join(ddir, os.path.basename(obj))
+                if stale(src, dobj):
+                    _compile(src, dobj, ["-DCTAP_DEBUG_BOUNDS", *extra], verbose)
+                dobjs.append(dobj)
+            else:
+                dobjs.append(obj)
+        if not os.path.exists(DEBUG_LIB) or \
+                any(os.path.getmtime(o) > os.path.getmtime(DEBUG_LIB) for o in dobjs):
+            _link(DEBUG_LIB, dobjs, verbose)
+    return LIB
+
+
+def _link(lib, objs, verbose):
+    cmd = ["nvcc", *ARCH, "-shared", "-o", lib + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
 
 
 if __name__ == "__main__":

@@ -37,6 +37,8 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "../../include/ctap.h"
+#include "bounds.cuh"
 #include "packed_passes.cuh"
 
 namespace ctap {
@@ -174,13 +176,60 @@ __device__ __forceinline__ void st_soa(float2 *p, const Q &v)
     *reinterpret_cast<float4 *>(p) = make_float4(v.x.x, v.x.y, v.y.x, v.y.y);
 }
 
+// Checked forms (bounds.cuh): off indexes float2 values of a buffer of lim
+// values; a 16-byte access covers off and off + 1.  Unchecked in the normal
+// build.
+template <int SITE> __device__ __forceinline__ Q ld_aos_c(const float2 *b, int off, int lim)
+{
+    Q v{};
+    if (CTAP_BOUNDS(SITE, off, lim - 1)) v = ld_aos(b + off);
+    return v;
+}
+template <int SITE> __device__ __forceinline__ Q ld_soa_c(const float2 *b, int off, int lim)
+{
+    Q v{};
+    if (CTAP_BOUNDS(SITE, off, lim - 1)) v = ld_soa(b + off);
+    return v;
+}
+template <int SITE> __device__ __forceinline__ void st_soa_c(float2 *b, int off, int lim, const Q &v)
+{
+    if (CTAP_BOUNDS(SITE, off, lim - 1)) st_soa(b + off, v);
+}
+template <int SITE> __device__ __forceinline__ float4 ld4_c(const float2 *b, int off, int lim)
+{
+    float4 v{};
+    if (CTAP_BOUNDS(SITE, off, lim - 1)) v = *reinterpret_cast<const float4 *>(b + off);
+    return v;
+}
+template <int SITE> __device__ __forceinline__ void st4_c(float2 *b, int off, int lim, const float4 &v)
+{
+    if (CTAP_BOUNDS(SITE, off, lim - 1)) *reinterpret_cast<float4 *>(b + off) = v;
+}
+template <int SITE> __device__ __forceinline__ float2 ld2_c(const float2 *b, int off, int lim)
+{
+    float2 v{};
+    if (CTAP_BOUNDS(SITE, off, lim)) v = b[off];
+    return v;
+}
+template <int SITE> __device__ __forceinline__ void st2_c(float2 *b, int off, int lim, const float2 &v)
+{
+    if (CTAP_BOUNDS(SITE, off, lim)) b[off] = v;
+}
+// table entry e of a table of n entries
+template <int SITE, class L> __device__ __forceinline__ L tab_c(const L *t, long long e, long long n)
+{
+    L v{};
+    if (CTAP_BOUNDS(SITE, e, n)) v = t[e];
+    return v;
+}
+
 // The thread index through an opaque move.  A mirror phase addresses the
 // same shared-memory positions (and table entries) as its forward phase;
 // taken from the plain index, the compiler keeps those values live from the
 // forward phase through every phase in between, which overflows the
 // 128-register budget of 512 threads into local memory.  The mirror phase
-// that closes the longest such span (A' in the Z pass, P3c in the XY pass)
-// takes its index through this move instead: measured no spills.
+// that closes the longest such span (A' in the Z pass, P5 in the XY pass)
+// takes its index through this move instead: no spills (ptxas -v).
 __device__ __forceinline__ int phase_tid()
 {
     int t;
@@ -221,6 +270,8 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
     const Geom &g = a.g;
     const Lift<T> *kxy = static_cast<const Lift<T> *>(a.kin_xy);
     const int t0 = threadIdx.x;
+    constexpr int RINGE = NRING * CHE;                 // float2 values in the ring
+    [[maybe_unused]] const long long NTOT = (long long)g.batch * g.rstride;   // float2 values of psi
     const int G = gridDim.x;
     const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
     const int nblk_mask = (1 << g.nblk_lg) - 1;
@@ -241,17 +292,18 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
         const int tile = blockIdx.x + i * G;
         const int tl = tile & ((1 << g.lgzt) - 1);
         const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
-        const float2 *src = a.src + (long long)(tile >> g.lgzt) * g.rstride +
-                            ((long long)(kp * P + cr) << g.lgnx) + b * W + 2 * ch +
-                            (long long)(c0 * CHZ + czl) * g.plane;
+        long long so = (long long)(tile >> g.lgzt) * g.rstride + ((long long)(kp * P + cr) << g.lgnx) +
+                       b * W + 2 * ch + (long long)(c0 * CHZ + czl) * g.plane;
         const long long zstep = (long long)(NT / 8) * g.plane;
         for (int c = c0; c < c1; ++c) {
             const int s = slot_of(i, c);
 #pragma unroll
             for (int m = 0; m < CHZ / (NT / 8); ++m) {
                 const int zz = c * CHZ + czl + m * (NT / 8);
-                cp_async16(ring + piece(s, zz, 2 * cr + ch), src);
-                src += zstep;
+                const int d = piece(s, zz, 2 * cr + ch);
+                if (CTAP_BOUNDS(1, d, RINGE - 1) && CTAP_BOUNDS(2, so, NTOT - 1))
+                    cp_async16(ring + d, a.src + so);
+                so += zstep;
             }
         }
     };
@@ -264,7 +316,7 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
             Lift<T> v;
             if (t < C) {
                 const int kx = b * W + (t & (W - 1)), ky = kp + ((t / W) << g.lgLy);
-                v = kxy[((long long)ky << g.lgnx) + kx];
+                v = tab_c<3>(kxy, ((long long)ky << g.lgnx) + kx, (long long)g.nx * g.ny);
             } else {
                 v = a.tw[g.cross_off + (((t - C + 1) * kp) & (g.ny - 1))];
             }
@@ -306,13 +358,13 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
             const int h = t & 1, zl = t >> 1;
             Lift<T> tw64[3];
 #pragma unroll
-            for (int k0 = 1; k0 < 4; ++k0) tw64[k0 - 1] = wz[16 * (zl >> 4) * k0];
+            for (int k0 = 1; k0 < 4; ++k0) tw64[k0 - 1] = tab_c<16>(wz, 16 * (zl >> 4) * k0, NZ);
             Q v[4][4];                                 // [a -> k0][r -> k2y]
 #pragma unroll
             for (int aa = 0; aa < 4; ++aa) {
                 const int zz = 256 * aa + zl;
 #pragma unroll
-                for (int r = 0; r < P; ++r) v[aa][r] = ld_aos(ring + piece(sl(zz / CHZ), zz, 2 * r + h));
+                for (int r = 0; r < P; ++r) v[aa][r] = ld_aos_c<4>(ring, piece(sl(zz / CHZ), zz, 2 * r + h), RINGE);
             }
 #pragma unroll
             for (int aa = 0; aa < 4; ++aa) {
@@ -336,7 +388,7 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
                     // twiddle of the next stage, exp(-2 pi i b k0/64), b = zl/16
                     if (k0 > 0) qlift_f(col[brev(k0, 4)], tw64[k0 - 1]);
                     const int zz = 256 * k0 + zl;
-                    st_soa(ring + piece(sl(zz / CHZ), zz, 2 * k2 + h), col[brev(k0, 4)]);
+                    st_soa_c<5>(ring, piece(sl(zz / CHZ), zz, 2 * k2 + h), RINGE, col[brev(k0, 4)]);
                 }
             }
         }
@@ -352,15 +404,15 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
 #pragma unroll
             for (int bb = 0; bb < 16; ++bb) {
                 const int zz = 256 * k0 + 16 * bb + c;
-                v[bb] = ld_soa(ring + piece(sl(zz / CHZ), zz, q));
+                v[bb] = ld_soa_c<6>(ring, piece(sl(zz / CHZ), zz, q), RINGE);
             }
             qdft_fwd<16, 0, 1>(v);
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) {
                 Q &w = v[brev(k1, 16)];
-                qlift_f(w, wz[c * (k0 + 4 * k1)]);
+                qlift_f(w, tab_c<7>(wz, c * (k0 + 4 * k1), NZ));
                 const int zz = 256 * k0 + 16 * k1 + c;
-                st_soa(ring + piece(sl(zz / CHZ), zz, q), w);
+                st_soa_c<8>(ring, piece(sl(zz / CHZ), zz, q), RINGE, w);
             }
         }
         if (more) issue(i + 1, 1, 2);
@@ -380,18 +432,18 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
             const float2 sxy = make_float2(tb[k2y * W + x0].s, tb[k2y * W + x0 + 1].s);
             Q v[16];
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc) v[cc] = ld_soa(ring + piece(s, zr + cc, q));
+            for (int cc = 0; cc < 16; ++cc) v[cc] = ld_soa_c<9>(ring, piece(s, zr + cc, q), RINGE);
             qdft_fwd<16, 0, 1>(v);                     // v[brev(k2)]: kz = m + 64 k2
 #pragma unroll
             for (int k2 = 0; k2 < 16; ++k2) {
-                const Lift<T> kk = kz[m + 64 * k2];
+                const Lift<T> kk = tab_c<10>(kz, m + 64 * k2, NZ);
                 Q &w = v[brev(k2, 16)];
                 qrot_f(w, pk(kk.p), pk(kk.u));
                 qscale(w, mul2(sxy, pk(kk.s)));
             }
             qdft_inv<16, 0, 1>(v);
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc) st_soa(ring + piece(s, zr + cc, q), v[cc]);
+            for (int cc = 0; cc < 16; ++cc) st_soa_c<11>(ring, piece(s, zr + cc, q), RINGE, v[cc]);
         }
         if (more) issue(i + 1, 2, 3);
         __syncthreads();
@@ -404,15 +456,15 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) {
                 const int zz = 256 * k0 + 16 * k1 + c;
-                Q w = ld_soa(ring + piece(sl(zz / CHZ), zz, q));
-                qlift_b(w, wz[c * (k0 + 4 * k1)]);
+                Q w = ld_soa_c<12>(ring, piece(sl(zz / CHZ), zz, q), RINGE);
+                qlift_b(w, tab_c<13>(wz, c * (k0 + 4 * k1), NZ));
                 v[brev(k1, 16)] = w;
             }
             qdft_inv<16, 0, 1>(v);
 #pragma unroll
             for (int bb = 0; bb < 16; ++bb) {
                 const int zz = 256 * k0 + 16 * bb + c;
-                st_soa(ring + piece(sl(zz / CHZ), zz, q), v[bb]);
+                st_soa_c<14>(ring, piece(sl(zz / CHZ), zz, q), RINGE, v[bb]);
             }
         }
         if (more) issue(i + 1, 3, 4);
@@ -433,14 +485,14 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
             for (int k0 = 0; k0 < 4; ++k0) {
                 const int zz = 256 * k0 + zl;
 #pragma unroll
-                for (int k2 = 0; k2 < P; ++k2) v[k0][k2] = ld_soa(ring + piece(sl(zz / CHZ), zz, 2 * k2 + h));
+                for (int k2 = 0; k2 < P; ++k2) v[k0][k2] = ld_soa_c<15>(ring, piece(sl(zz / CHZ), zz, 2 * k2 + h), RINGE);
             }
             Lift<T> cw[P];
 #pragma unroll
             for (int r = 1; r < P; ++r) cw[r] = tb[C + r - 1];
             Lift<T> tw64[3];
 #pragma unroll
-            for (int k0 = 1; k0 < 4; ++k0) tw64[k0 - 1] = wz[16 * (zl >> 4) * k0];
+            for (int k0 = 1; k0 < 4; ++k0) tw64[k0 - 1] = tab_c<16>(wz, 16 * (zl >> 4) * k0, NZ);
             __syncthreads();                           // every slot of tile i is free
             if (more) issue(i + 1, NCH / 2, NCH);
             cp_async_commit();
@@ -465,11 +517,14 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
 #pragma unroll
                 for (int r = 1; r < P; ++r) qlift_b(row[r], cw[r]);
                 const int zz = 256 * aa + zl;
-                float2 *p = a.dst + colbase + (long long)zz * g.plane + 2 * h;
+                const long long po = colbase + (long long)zz * g.plane + 2 * h;
 #pragma unroll
-                for (int r = 0; r < P; ++r)
-                    __stcs(reinterpret_cast<float4 *>(p + ((long long)r << g.lgnx)),
-                           make_float4(row[r].x.x, row[r].y.x, row[r].x.y, row[r].y.y));
+                for (int r = 0; r < P; ++r) {
+                    const long long o = po + ((long long)r << g.lgnx);
+                    if (CTAP_BOUNDS(17, o, NTOT - 1))
+                        __stcs(reinterpret_cast<float4 *>(a.dst + o),
+                               make_float4(row[r].x.x, row[r].y.x, row[r].x.y, row[r].y.y));
+                }
             }
         }
     }
@@ -546,20 +601,23 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
     const int G = gridDim.x;
     const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
     const T tau = k.tau_full;
+    constexpr int BUFE = 3 * HB;                       // float2 values in the half buffers
+    [[maybe_unused]] const long long NTOT = (long long)g.batch * g.rstride;
     auto unswx = [](int q) { return q / RA + RB * (q % RA); };
     auto half_buf = [&](int i, int h) { return bufs + ((2 * i + h) % 3) * HB; };
     const int cpiece = t0 % PPR, crow = t0 / PPR;
     auto issue = [&](int i, int h, int m0, int m1) {
         const int tile = blockIdx.x + i * G;
         const int z = tile >> g.lgP, r = tile & (g.P - 1);
-        const float2 *src = a.src + (long long)z * g.plane +
-                            ((long long)((h * HR + crow + RPI * m0) * g.P + r) << g.lgnx) + 2 * cpiece;
-        float2 *dst = half_buf(i, h) + (crow + RPI * m0) * PITCH + 2 * cpiece;
+        long long so = (long long)z * g.plane + ((long long)((h * HR + crow + RPI * m0) * g.P + r) << g.lgnx) +
+                       2 * cpiece;
+        int d = (int)(half_buf(i, h) - bufs) + (crow + RPI * m0) * PITCH + 2 * cpiece;
         const long long rstep = (long long)(RPI * g.P) << g.lgnx;
         for (int m = m0; m < m1; ++m) {
-            cp_async16(dst, src);
-            src += rstep;
-            dst += RPI * PITCH;
+            if (CTAP_BOUNDS(21, d, BUFE - 1) && CTAP_BOUNDS(22, so, NTOT - 1))
+                cp_async16(bufs + d, a.src + so);
+            so += rstep;
+            d += RPI * PITCH;
         }
     };
     auto load_tabs = [&](int i) {
@@ -589,28 +647,28 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
         if (more) load_tabs(i + 1);
         cp_async_wait_all();
         __syncthreads();                         // tile i (and its tables) visible
-        float2 *const b0 = half_buf(i, 0);
-        float2 *const b1 = half_buf(i, 1);
+        // offsets (float2 values) of the tile's two half buffers
+        const int o0 = (int)(half_buf(i, 0) - bufs), o1 = (int)(half_buf(i, 1) - bufs);
 
         // P1: inverse x, last stage (radix RB), rows rw and rw + 32 as a pair;
         //     AoS in, split out
         {
             const int t = threadIdx.x;
             const int j = t & 15, rw = t >> 4;
-            float2 *pa = b0 + rw * PITCH, *pb = b1 + rw * PITCH;
+            const int pa = o0 + rw * PITCH + j, pb = o1 + rw * PITCH + j;
             Q v[RB];
 #pragma unroll
             for (int kk = 0; kk < RB; ++kk) {
-                const float2 ea = pa[j + RA * kk], eb = pb[j + RA * kk];
+                const float2 ea = ld2_c<23>(bufs, pa + RA * kk, BUFE), eb = ld2_c<23>(bufs, pb + RA * kk, BUFE);
                 v[brev(kk, RB)] = Q{make_float2(ea.x, eb.x), make_float2(ea.y, eb.y)};
             }
             qdft_inv<RB, 0, 1>(v);
 #pragma unroll
-            for (int rr = 1; rr < RB; ++rr) qlift_b(v[rr], wx[rr * RA + j]);
+            for (int rr = 1; rr < RB; ++rr) qlift_b(v[rr], tab_c<24>(wx, rr * RA + j, NX));
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) {
-                pa[j + RA * rr] = v[rr].x;
-                pb[j + RA * rr] = v[rr].y;
+                st2_c<25>(bufs, pa + RA * rr, BUFE, v[rr].x);
+                st2_c<25>(bufs, pb + RA * rr, BUFE, v[rr].y);
             }
         }
         if (more) issue(i + 1, 0, 0, 2);
@@ -621,27 +679,27 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
         {
             const int t = threadIdx.x;
             const int rw = t & 31, j = t >> 5;
-            float2 *pa = b0 + rw * PITCH + RA * j, *pb = b1 + rw * PITCH + RA * j;
+            const int pa = o0 + rw * PITCH + RA * j, pb = o1 + rw * PITCH + RA * j;
             Q v[RA];
 #pragma unroll
             for (int m = 0; m < RA; m += 2) {
-                const float4 xr = *reinterpret_cast<const float4 *>(pa + m);
-                const float4 xi = *reinterpret_cast<const float4 *>(pb + m);
+                const float4 xr = ld4_c<26>(bufs, pa + m, BUFE);
+                const float4 xi = ld4_c<26>(bufs, pb + m, BUFE);
                 v[brev(m, RA)] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
                 v[brev(m + 1, RA)] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
             }
             qdft_inv<RA, 0, 1>(v);
 #pragma unroll
             for (int m = 0; m < RA; m += 2) {
-                *reinterpret_cast<float4 *>(pa + m) = make_float4(v[m].x.x, v[m + 1].x.x, v[m].y.x, v[m + 1].y.x);
-                *reinterpret_cast<float4 *>(pb + m) = make_float4(v[m].x.y, v[m + 1].x.y, v[m].y.y, v[m + 1].y.y);
+                st4_c<27>(bufs, pa + m, BUFE, make_float4(v[m].x.x, v[m + 1].x.x, v[m].y.x, v[m + 1].y.x));
+                st4_c<27>(bufs, pb + m, BUFE, make_float4(v[m].x.y, v[m + 1].x.y, v[m].y.y, v[m + 1].y.y));
             }
         }
         if (more) issue(i + 1, 0, 2, 4);
         __syncthreads();
 
         // row ii + YA kk (kk < YB) of the tile, at column piece q (16 bytes)
-        auto yrow = [&](int row, int q) { return (row < HR ? b0 : b1) + (row % HR) * PITCH + 2 * q; };
+        auto yrow = [&](int row, int q) { return (row < HR ? o0 : o1) + (row % HR) * PITCH + 2 * q; };
 
         // P3a: inverse y, last stage (radix YB) on rows ii + YA kk, two
         //      column pairs (pieces pp and pp + 64)
@@ -651,21 +709,21 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
             Q v[2][YB];
 #pragma unroll
             for (int kk = 0; kk < YB; ++kk) {
-                v[0][brev(kk, YB)] = ld_soa(yrow(ii + YA * kk, pp));
-                v[1][brev(kk, YB)] = ld_soa(yrow(ii + YA * kk, pp + 64));
+                v[0][brev(kk, YB)] = ld_soa_c<28>(bufs, yrow(ii + YA * kk, pp), BUFE);
+                v[1][brev(kk, YB)] = ld_soa_c<28>(bufs, yrow(ii + YA * kk, pp + 64), BUFE);
             }
             qdft_inv<YB, 0, 1>(v[0]);
             qdft_inv<YB, 0, 1>(v[1]);
 #pragma unroll
             for (int rr = 1; rr < YB; ++rr) {
-                const Lift<T> tw = wy[ii * rr];
+                const Lift<T> tw = tab_c<33>(wy, ii * rr, LY);
                 qlift_b(v[0][rr], tw);
                 qlift_b(v[1][rr], tw);
             }
 #pragma unroll
             for (int rr = 0; rr < YB; ++rr) {
-                st_soa(yrow(ii + YA * rr, pp), v[0][rr]);
-                st_soa(yrow(ii + YA * rr, pp + 64), v[1][rr]);
+                st_soa_c<29>(bufs, yrow(ii + YA * rr, pp), BUFE, v[0][rr]);
+                st_soa_c<29>(bufs, yrow(ii + YA * rr, pp + 64), BUFE, v[1][rr]);
             }
         }
         if (more) issue(i + 1, 0, 4, 6);
@@ -681,8 +739,8 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
             Q v[2][YA];
 #pragma unroll
             for (int kk = 0; kk < YA; ++kk) {
-                v[0][brev(kk, YA)] = ld_soa(yrow(YA * ii + kk, pp));
-                v[1][brev(kk, YA)] = ld_soa(yrow(YA * ii + kk, pp + 64));
+                v[0][brev(kk, YA)] = ld_soa_c<30>(bufs, yrow(YA * ii + kk, pp), BUFE);
+                v[1][brev(kk, YA)] = ld_soa_c<30>(bufs, yrow(YA * ii + kk, pp + 64), BUFE);
             }
             qdft_inv<YA, 0, 1>(v[0]);
             qdft_inv<YA, 0, 1>(v[1]);
@@ -701,8 +759,8 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
             qdft_fwd<YA, 0, 1>(v[1]);
 #pragma unroll
             for (int kk = 0; kk < YA; ++kk) {
-                st_soa(yrow(YA * ii + kk, pp), v[0][brev(kk, YA)]);
-                st_soa(yrow(YA * ii + kk, pp + 64), v[1][brev(kk, YA)]);
+                st_soa_c<31>(bufs, yrow(YA * ii + kk, pp), BUFE, v[0][brev(kk, YA)]);
+                st_soa_c<31>(bufs, yrow(YA * ii + kk, pp + 64), BUFE, v[1][brev(kk, YA)]);
             }
         }
         if (more) issue(i + 1, 0, 6, 8);
@@ -712,17 +770,17 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
         // P3c: forward y, last stage (radix YB) on rows ii + YA rr; column
         //      pairs in, split out (rows ii + YA m and ii + YA m + 32 pair up)
         {
-            const int t = phase_tid();
+            const int t = threadIdx.x;
             const int pp = t & 63, ii = t >> 6;
             Q v[2][YB];
 #pragma unroll
             for (int rr = 0; rr < YB; ++rr) {
-                v[0][rr] = ld_soa(yrow(ii + YA * rr, pp));
-                v[1][rr] = ld_soa(yrow(ii + YA * rr, pp + 64));
+                v[0][rr] = ld_soa_c<32>(bufs, yrow(ii + YA * rr, pp), BUFE);
+                v[1][rr] = ld_soa_c<32>(bufs, yrow(ii + YA * rr, pp + 64), BUFE);
             }
 #pragma unroll
             for (int rr = 1; rr < YB; ++rr) {
-                const Lift<T> tw = wy[ii * rr];
+                const Lift<T> tw = tab_c<33>(wy, ii * rr, LY);
                 qlift_f(v[0][rr], tw);
                 qlift_f(v[1][rr], tw);
             }
@@ -737,8 +795,8 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
                 for (int c = 0; c < 2; ++c) {
                     const Q &qa = v[c][brev(mm, YB)], &qb = v[c][brev(mm + YB / 2, YB)];
                     const int off = lr * PITCH + 2 * (pp + 64 * c);
-                    *reinterpret_cast<float4 *>(b0 + off) = make_float4(qa.x.x, qb.x.x, qa.x.y, qb.x.y);
-                    *reinterpret_cast<float4 *>(b1 + off) = make_float4(qa.y.x, qb.y.x, qa.y.y, qb.y.y);
+                    st4_c<34>(bufs, o0 + off, BUFE, make_float4(qa.x.x, qb.x.x, qa.x.y, qb.x.y));
+                    st4_c<34>(bufs, o1 + off, BUFE, make_float4(qa.y.x, qb.y.x, qa.y.y, qb.y.y));
                 }
             }
         }
@@ -748,12 +806,12 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
         {
             const int t = threadIdx.x;
             const int rw = t & 31, j = t >> 5;
-            float2 *pa = b0 + rw * PITCH + RA * j, *pb = b1 + rw * PITCH + RA * j;
+            const int pa = o0 + rw * PITCH + RA * j, pb = o1 + rw * PITCH + RA * j;
             Q v[RA];
 #pragma unroll
             for (int m = 0; m < RA; m += 2) {
-                const float4 xr = *reinterpret_cast<const float4 *>(pa + m);
-                const float4 xi = *reinterpret_cast<const float4 *>(pb + m);
+                const float4 xr = ld4_c<35>(bufs, pa + m, BUFE);
+                const float4 xi = ld4_c<35>(bufs, pb + m, BUFE);
                 v[m] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
                 v[m + 1] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
             }
@@ -761,8 +819,8 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
 #pragma unroll
             for (int m = 0; m < RA; m += 2) {
                 const Q &e0 = v[brev(m, RA)], &e1 = v[brev(m + 1, RA)];
-                *reinterpret_cast<float4 *>(pa + m) = make_float4(e0.x.x, e0.x.y, e1.x.x, e1.x.y);
-                *reinterpret_cast<float4 *>(pb + m) = make_float4(e0.y.x, e0.y.y, e1.y.x, e1.y.y);
+                st4_c<36>(bufs, pa + m, BUFE, make_float4(e0.x.x, e0.x.y, e1.x.x, e1.x.y));
+                st4_c<36>(bufs, pb + m, BUFE, make_float4(e0.y.x, e0.y.y, e1.y.x, e1.y.y));
             }
         }
         __syncthreads();
@@ -770,25 +828,26 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
         // P5: forward x, last stage, to HBM.  The task is read back first so
         //     that both half buffers can take the next tile's second half.
         {
-            const int t = threadIdx.x;
+            const int t = phase_tid();
             const int j = t & 15, rw = t >> 4;
             Q v[RB];
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr)
-                v[rr] = Q{b0[rw * PITCH + j + RA * rr], b1[rw * PITCH + j + RA * rr]};
+                v[rr] = Q{ld2_c<37>(bufs, o0 + rw * PITCH + j + RA * rr, BUFE),
+                          ld2_c<37>(bufs, o1 + rw * PITCH + j + RA * rr, BUFE)};
             __syncthreads();                     // tile i's buffers are free
             if (more) issue(i + 1, 1, 0, NCR);
             cp_async_commit();
 #pragma unroll
-            for (int rr = 1; rr < RB; ++rr) qlift_f(v[rr], wx[rr * RA + j]);
+            for (int rr = 1; rr < RB; ++rr) qlift_f(v[rr], tab_c<24>(wx, rr * RA + j, NX));
             qdft_fwd<RB, 0, 1>(v);
-            float2 *oa = a.dst + (long long)z * g.plane + ((long long)(rw * g.P + r) << g.lgnx) + j;
-            float2 *ob = oa + ((long long)(HR * g.P) << g.lgnx);
+            const long long oa = (long long)z * g.plane + ((long long)(rw * g.P + r) << g.lgnx) + j;
+            const long long ob = oa + ((long long)(HR * g.P) << g.lgnx);
 #pragma unroll
             for (int k2 = 0; k2 < RB; ++k2) {
                 const Q &e = v[brev(k2, RB)];
-                oa[RA * k2] = make_float2(e.x.x, e.y.x);
-                ob[RA * k2] = make_float2(e.x.y, e.y.y);
+                if (CTAP_BOUNDS(38, oa + RA * k2, NTOT)) a.dst[oa + RA * k2] = make_float2(e.x.x, e.y.x);
+                if (CTAP_BOUNDS(38, ob + RA * k2, NTOT)) a.dst[ob + RA * k2] = make_float2(e.x.y, e.y.y);
             }
         }
     }
@@ -832,6 +891,37 @@ bool launch_xy_packed(const XYArgs<float> &a, cudaStream_t st)
         xy_pk_kernel<1><<<grid, kXpkNT, smem, st>>>(a, ntiles);
     return true;
 }
+
+}  // namespace ctap
+
+// Record of the bounds-checked build (bounds.cuh): the checked kernels live
+// in this file, so does their record.
+extern "C" ctap_status ctap_debug_bounds(int clear, long long *out)
+{
+    if (!out) return CTAP_ERR_INVALID_ARG;
+#ifdef CTAP_DEBUG_BOUNDS
+    unsigned long long v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpyFromSymbol(&v, g_ctap_bounds, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return CTAP_ERR_CUDA;
+    }
+    if (clear) {
+        const unsigned long long zero = 0;
+        if (cudaMemcpyToSymbol(g_ctap_bounds, &zero, sizeof zero) != cudaSuccess) {
+            cudaGetLastError();
+            return CTAP_ERR_CUDA;
+        }
+    }
+    *out = (long long)v;
+#else
+    (void)clear;
+    *out = -1;
+#endif
+    return CTAP_OK;
+}
+
+namespace ctap {
 
 bool packed_z_supported(const Geom &g)
 {

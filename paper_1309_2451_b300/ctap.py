@@ -10,7 +10,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libctap.so")
+# CTAP_LIB=debug selects the bounds-checked build (build.build(debug=True))
+LIB_PATH = os.path.join(_HERE, "libctap_debug.so" if os.environ.get("CTAP_LIB") == "debug"
+                        else "libctap.so")
 
 CTAP_C64, CTAP_C128, CTAP_C128_DF = 0, 1, 2
 CTAP_REAL, CTAP_IMAG, CTAP_REAL_KVK = 0, 1, 2
@@ -64,6 +66,7 @@ def lib():
         "ctap_plan_info": [_vp, ctypes.POINTER(ll)],
         "ctap_norm_noalloc": [_vp, ll, i, d, _vp, _vp],
         "ctap_measure_fma_peaks": [_vp, _dp],
+        "ctap_debug_bounds": [i, ctypes.POINTER(ll)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -87,7 +90,8 @@ def exported_symbols():
             "ctap_set_profiling", "ctap_pass_times", "ctap_plan_info", "ctap_status_string",
             "ctap_last_error", "ctap_version", "ctap_norm_noalloc", "ctap_add_potential_z",
             "ctap_density_xz", "ctap_plan_create_batched", "ctap_set_guides_batched",
-            "ctap_set_potential_wires", "ctap_measure_fma_peaks"]
+            "ctap_set_potential_wires", "ctap_measure_fma_peaks",
+            "ctap_debug_bounds"]
 
 
 def _f64(a, n=None):
@@ -312,6 +316,16 @@ def ctap_adjoint_apply(c12, c23, plan, psi0, nsteps, dt, K=32, guide=3, V0=20.0,
         _CtapAdjoint = _adjoint_function()
     return _CtapAdjoint.apply(c12, c23, plan, psi0, nsteps, dt, K, guide, V0, s, knots,
                               halfwidth)
+
+
+def debug_bounds(clear=True):
+    """Record of the bounds-checked build: 0 (no violation), site << 48 |
+    index of the first violation, or -1 for a build without checks."""
+    v = ctypes.c_longlong()
+    rc = lib().ctap_debug_bounds(1 if clear else 0, ctypes.byref(v))
+    if rc != 0:
+        raise CtapError(rc, "ctap_debug_bounds")
+    return v.value
 
 
 def measure_fma_peaks(stream=None):
