@@ -228,8 +228,9 @@ template <int SITE, class L> __device__ __forceinline__ L tab_c(const L *t, long
 // taken from the plain index, the compiler keeps those values live from the
 // forward phase through every phase in between, which overflows the
 // 128-register budget of 512 threads into local memory.  The mirror phase
-// that closes the longest such span (A' in the Z pass, P5 in the XY pass)
-// takes its index through this move instead: no spills (ptxas -v).
+// phases that close the longest such spans (B' and A' in the Z pass, P5 in
+// the XY pass, A' in the five-bit XY pass) take their index through this
+// move instead: no spills (ptxas -v).
 __device__ __forceinline__ int phase_tid()
 {
     int t;
@@ -282,8 +283,15 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
         s -= (s >= NRING) ? NRING : 0;
         return s;
     };
-    // element offset of piece q (columns 2q, 2q + 1) of z-row zz in chunk slot s
-    auto piece = [](int s, int zz, int q) { return s * CHE + (zz % CHZ) * C + 2 * (q ^ (zz & 7)); };
+    // element offset of piece q (columns 2q, 2q + 1) of z-row zz in chunk slot
+    // s.  Swizzle: the 32-byte group of a row class moves with z mod 4 and
+    // its 16-byte halves swap with bit 2 of z.  A 16-byte shared access is
+    // served eight lanes at a time; the eight lanes of phases A and A' are
+    // four z-rows x two halves, of phases B and C and of the copies one
+    // z-row's eight pieces: every group meets eight distinct bank groups.
+    auto piece = [](int s, int zz, int q) {
+        return s * CHE + (zz % CHZ) * C + 2 * (q ^ (((zz & 3) << 1) | ((zz >> 2) & 1)));
+    };
 
     // asynchronous copy of chunks [c0, c1) of the i-th tile: thread t moves
     // piece (row class r, half h) of z-rows czl + 64 m of each chunk
@@ -450,7 +458,7 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
 
         // ---- B': mirror of B
         {
-            const int t = threadIdx.x;
+            const int t = phase_tid();
             const int q = t & 7, c = (t >> 3) & 15, k0 = t >> 7;
             Q v[16];
 #pragma unroll
@@ -854,6 +862,285 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
     cp_async_wait_all();
 }
 
+// ======================================================== XY (packed, 5-bit)
+// The same steady XY pass in three register phases per direction instead of
+// four, so a tile passes through shared memory 10 times instead of 14:
+//   x = 16 x1 + x2, kx = k1 + 16 k2 (as xy_pk_kernel); y = 2 j1 + j2 (j1 < 32),
+//   k' = k1 + 32 k2 (k2 < 2)
+//   A   inverse x, last stage (radix 16 over k2 for fixed k1, from the ring,
+//       rows rw and rw + 32 paired), inverse twiddle exp(2 pi i x2 k1/256);
+//   B   inverse x, first stage (radix 16 over the 16 contiguous positions of
+//       one x2) and inverse y, last stage (radix 2 over the rows k1, k1 + 32)
+//       with the inverse twiddle exp(2 pi i j2 k1/64);
+//   C   inverse y, first stage (radix 32 over the 32 rows of one half buffer),
+//       the potential factor, forward radix 32;
+//   B', A' the mirrors (A' stores to HBM).
+// 256 threads, 64 complex values (32 pairs) per thread in B and C, two
+// 32-value tasks in A and A'.  Pairs: A and A' pair rows rw and rw + 32; B,
+// C and B' pair positions p and p + 128 of one row, kept "split" in shared
+// memory: the pair of real parts at position p, the pair of imaginary parts
+// at position p + 128.
+constexpr int kX5NT = 256;
+
+template <int TIER>
+__global__ void __launch_bounds__(kX5NT, 1) xy5_kernel(const XYArgs<float> a, int ntiles)
+{
+    constexpr int NX = 256, LY = 64, NT = kX5NT;
+    constexpr int PITCH = NX + 2;                // complex values per row (16-byte rows)
+    constexpr int HR = LY / 2;                   // rows per half buffer
+    constexpr int HB = HR * PITCH;               // complex values per half buffer
+    constexpr int PPR = NX / 2;                  // 16-byte pieces per row
+    constexpr int RPI = NT / PPR;                // rows per copy round (2)
+    constexpr int NCR = HR / RPI;                // copy rounds per half (16)
+    using T = float;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *bufs = reinterpret_cast<float2 *>(smraw);
+    Lift<T> *wx = reinterpret_cast<Lift<T> *>(bufs + 3 * HB);   // [x2 16 + k1] = exp(-2 pi i k1 x2/256)
+    Lift<T> *wy = wx + NX;                                      // exp(-2 pi i e/64)
+    __shared__ T gtab[2][LY];                    // g(y), y = r + P j, per tile
+    __shared__ float2 htab[2][NX / 2];           // H(x(p), z) tau and H(x(p + 128), z) tau
+    __shared__ T thzs[2];
+
+    const Geom &g = a.g;
+    const Kick<T> &k = a.k;
+    const int t0 = threadIdx.x;
+    const int G = gridDim.x;
+    const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
+    const T tau = k.tau_full;
+    constexpr int BUFE = 3 * HB;
+    [[maybe_unused]] const long long NTOT = (long long)g.batch * g.rstride;
+    auto unswx = [](int q) { return q / 16 + 16 * (q % 16); };       // position -> x
+    auto half_buf = [&](int i, int h) { return ((2 * i + h) % 3) * HB; };
+    const int cpiece = t0 % PPR, crow = t0 / PPR;
+    auto issue = [&](int i, int h, int m0, int m1) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        long long so = (long long)z * g.plane + ((long long)((h * HR + crow + RPI * m0) * g.P + r) << g.lgnx) +
+                       2 * cpiece;
+        int d = half_buf(i, h) + (crow + RPI * m0) * PITCH + 2 * cpiece;
+        const long long rstep = (long long)(RPI * g.P) << g.lgnx;
+        for (int m = m0; m < m1; ++m) {
+            if (CTAP_BOUNDS(41, d, BUFE - 1) && CTAP_BOUNDS(42, so, NTOT - 1))
+                cp_async16(bufs + d, a.src + so);
+            so += rstep;
+            d += RPI * PITCH;
+        }
+    };
+    auto load_tabs = [&](int i) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        if (t0 < LY) gtab[i & 1][t0] = k.g[r + t0 * g.P];
+        if (t0 < NX / 2) {
+            const long long hz = (long long)z * g.nx;
+            htab[i & 1][t0] = make_float2(k.H[hz + unswx(t0)] * tau, k.H[hz + unswx(t0 + NX / 2)] * tau);
+        }
+        if (t0 == 0) thzs[i & 1] = k.vz ? k.vz[z & (g.nz - 1)] * tau : T(0);
+    };
+
+    if (nmine > 0) {
+        issue(0, 0, 0, NCR);
+        issue(0, 1, 0, NCR);
+        load_tabs(0);
+    }
+    cp_async_commit();
+    for (int e = t0; e < NX + LY; e += NT)
+        wx[e] = e < NX ? a.tw[g.fast_x_off + (e % 16) * (e / 16)] : a.tw[g.fast_y_off + e - NX];
+
+    for (int i = 0; i < nmine; ++i) {
+        const int tile = blockIdx.x + i * G;
+        const int z = tile >> g.lgP, r = tile & (g.P - 1);
+        const bool more = i + 1 < nmine;
+        if (more) load_tabs(i + 1);
+        cp_async_wait_all();
+        __syncthreads();
+        const int o0 = half_buf(i, 0), o1 = half_buf(i, 1);
+
+        // A: inverse x last stage on rows (rw, rw + 32); AoS in, position
+        //    pairs (p, p + 128) out, split
+#pragma unroll 1
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int q = threadIdx.x + NT * s2;
+            const int k1 = q & 15, rw = q >> 4;
+            const int pa = o0 + rw * PITCH + k1, pb = o1 + rw * PITCH + k1;
+            Q v[16];
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                const float2 ea = ld2_c<43>(bufs, pa + 16 * kk, BUFE), eb = ld2_c<43>(bufs, pb + 16 * kk, BUFE);
+                v[brev(kk, 16)] = Q{make_float2(ea.x, eb.x), make_float2(ea.y, eb.y)};
+            }
+            qdft_inv<16, 0, 1>(v);
+#pragma unroll
+            for (int x2 = 1; x2 < 16; ++x2) qlift_b(v[x2], tab_c<44>(wx, x2 * 16 + k1, NX));
+#pragma unroll
+            for (int x2 = 0; x2 < 8; ++x2) {
+                const Q &u = v[x2], &w = v[x2 + 8];
+                st2_c<45>(bufs, pa + 16 * x2, BUFE, make_float2(u.x.x, w.x.x));
+                st2_c<45>(bufs, pa + 16 * x2 + 128, BUFE, make_float2(u.y.x, w.y.x));
+                st2_c<45>(bufs, pb + 16 * x2, BUFE, make_float2(u.x.y, w.x.y));
+                st2_c<45>(bufs, pb + 16 * x2 + 128, BUFE, make_float2(u.y.y, w.y.y));
+            }
+        }
+        if (more) issue(i + 1, 0, 0, 4);
+        __syncthreads();
+
+        // B: inverse x first stage (16 contiguous positions of x2 and of
+        //    x2 + 8) and inverse y last stage (rows k1, k1 + 32), in place
+        {
+            const int t = threadIdx.x;
+            const int k1 = t & 31, x2 = t >> 5;
+            const int ra = o0 + k1 * PITCH + 16 * x2, rb = o1 + k1 * PITCH + 16 * x2;
+            Q v[2][16];                                // [k2][x position]
+#pragma unroll
+            for (int m = 0; m < 16; m += 2) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ro = h ? rb : ra;
+                    const float4 xr = ld4_c<46>(bufs, ro + m, BUFE), xi = ld4_c<46>(bufs, ro + m + 128, BUFE);
+                    v[h][brev(m, 16)] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
+                    v[h][brev(m + 1, 16)] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
+                }
+            }
+            qdft_inv<16, 0, 1>(v[0]);
+            qdft_inv<16, 0, 1>(v[1]);
+            const Lift<T> wyk = tab_c<47>(wy, k1, LY);
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {             // radix 2 over k2, then exp(2 pi i j2 k1/64)
+                const Q s0 = qadd(v[0][m], v[1][m]);
+                Q s1 = qsub(v[0][m], v[1][m]);
+                qlift_b(s1, wyk);
+                v[0][m] = s0;
+                v[1][m] = s1;
+            }
+#pragma unroll
+            for (int m = 0; m < 16; m += 2) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ro = h ? rb : ra;
+                    st4_c<48>(bufs, ro + m, BUFE, make_float4(v[h][m].x.x, v[h][m].x.y, v[h][m + 1].x.x, v[h][m + 1].x.y));
+                    st4_c<48>(bufs, ro + m + 128, BUFE, make_float4(v[h][m].y.x, v[h][m].y.y, v[h][m + 1].y.x, v[h][m + 1].y.y));
+                }
+            }
+        }
+        if (more) issue(i + 1, 0, 4, 8);
+        __syncthreads();
+
+        // C: inverse y first stage (radix 32 over the rows of half buffer j2)
+        //    -> potential factor -> forward radix 32, column pair (p, p + 128)
+        {
+            const int t = threadIdx.x;
+            const int pp = t & 127, j2 = t >> 7;
+            const int base = (j2 ? o1 : o0) + pp;
+            const T *gt = gtab[i & 1];
+            const T thz = thzs[i & 1];
+            const float2 hx = htab[i & 1][pp];
+            Q v[32];
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1)
+                v[brev(k1, 32)] = Q{ld2_c<49>(bufs, base + k1 * PITCH, BUFE), ld2_c<49>(bufs, base + k1 * PITCH + 128, BUFE)};
+            qdft_inv<32, 0, 1>(v);                     // v[j1]: real row j = 2 j1 + j2
+#pragma unroll
+            for (int j1 = 0; j1 < 32; ++j1) {
+                float2 p, u;
+                qkick_coef<TIER>(fma2(pk(gt[2 * j1 + j2]), hx, pk(thz)), p, u);
+                qrot_f(v[j1], p, u);
+            }
+            qdft_fwd<32, 0, 1>(v);
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1) {
+                st2_c<50>(bufs, base + k1 * PITCH, BUFE, v[brev(k1, 32)].x);
+                st2_c<50>(bufs, base + k1 * PITCH + 128, BUFE, v[brev(k1, 32)].y);
+            }
+        }
+        if (more) issue(i + 1, 0, 8, 12);
+        __syncthreads();
+
+        // B': mirror of B
+        {
+            const int t = threadIdx.x;
+            const int k1 = t & 31, x2 = t >> 5;
+            const int ra = o0 + k1 * PITCH + 16 * x2, rb = o1 + k1 * PITCH + 16 * x2;
+            Q v[2][16];
+#pragma unroll
+            for (int m = 0; m < 16; m += 2) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ro = h ? rb : ra;
+                    const float4 xr = ld4_c<51>(bufs, ro + m, BUFE), xi = ld4_c<51>(bufs, ro + m + 128, BUFE);
+                    v[h][m] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
+                    v[h][m + 1] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
+                }
+            }
+            const Lift<T> wyk = tab_c<52>(wy, k1, LY);
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                Q s1 = v[1][m];
+                qlift_f(s1, wyk);
+                const Q s0 = v[0][m];
+                v[0][m] = qadd(s0, s1);
+                v[1][m] = qsub(s0, s1);
+            }
+            qdft_fwd<16, 0, 1>(v[0]);
+            qdft_fwd<16, 0, 1>(v[1]);
+#pragma unroll
+            for (int m = 0; m < 16; m += 2) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ro = h ? rb : ra;
+                    const Q &e0 = v[h][brev(m, 16)], &e1 = v[h][brev(m + 1, 16)];
+                    st4_c<53>(bufs, ro + m, BUFE, make_float4(e0.x.x, e0.x.y, e1.x.x, e1.x.y));
+                    st4_c<53>(bufs, ro + m + 128, BUFE, make_float4(e0.y.x, e0.y.y, e1.y.x, e1.y.y));
+                }
+            }
+        }
+        if (more) issue(i + 1, 0, 12, 16);
+        cp_async_commit();
+        __syncthreads();
+
+        // A': read both tasks back (frees both half buffers), then the mirror
+        //     of A and the stores to HBM
+        {
+            const int t = phase_tid();
+            Q v[2][16];
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int q = t + NT * s2;
+                const int k1 = q & 15, rw = q >> 4;
+                const int pa = o0 + rw * PITCH + k1, pb = o1 + rw * PITCH + k1;
+#pragma unroll
+                for (int x2 = 0; x2 < 8; ++x2) {
+                    const float2 ra = ld2_c<54>(bufs, pa + 16 * x2, BUFE), ia = ld2_c<54>(bufs, pa + 16 * x2 + 128, BUFE);
+                    const float2 rb = ld2_c<54>(bufs, pb + 16 * x2, BUFE), ib = ld2_c<54>(bufs, pb + 16 * x2 + 128, BUFE);
+                    v[s2][x2] = Q{make_float2(ra.x, rb.x), make_float2(ia.x, ib.x)};
+                    v[s2][x2 + 8] = Q{make_float2(ra.y, rb.y), make_float2(ia.y, ib.y)};
+                }
+            }
+            __syncthreads();                           // tile i's buffers are free
+            if (more) issue(i + 1, 1, 0, NCR);
+            cp_async_commit();
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {                // unrolled: v[s2] stays in registers
+                const int q = t + NT * s2;
+                const int k1 = q & 15, rw = q >> 4;
+                Q w[16];
+#pragma unroll
+                for (int x2 = 0; x2 < 16; ++x2) w[x2] = v[s2][x2];
+#pragma unroll
+                for (int x2 = 1; x2 < 16; ++x2) qlift_f(w[x2], tab_c<55>(wx, x2 * 16 + k1, NX));
+                qdft_fwd<16, 0, 1>(w);
+                const long long oa = (long long)z * g.plane + ((long long)(rw * g.P + r) << g.lgnx) + k1;
+                const long long ob = oa + ((long long)(HR * g.P) << g.lgnx);
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) {
+                    const Q &e = w[brev(k2, 16)];
+                    if (CTAP_BOUNDS(56, oa + 16 * k2, NTOT)) a.dst[oa + 16 * k2] = make_float2(e.x.x, e.y.x);
+                    if (CTAP_BOUNDS(56, ob + 16 * k2, NTOT)) a.dst[ob + 16 * k2] = make_float2(e.x.y, e.y.y);
+                }
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
 // ================================================================ dispatch
 namespace {
 int pk_sm_count()
@@ -885,6 +1172,24 @@ bool launch_xy_packed(const XYArgs<float> &a, cudaStream_t st)
     }
     const int ntiles = xy_grid(a.g);
     const int grid = std::min(ntiles, pk_sm_count());
+    // the five-bit pass by default; CTAP_XY5=0 keeps the four-bit pass
+    static const bool five = [] {
+        const char *e = std::getenv("CTAP_XY5");
+        return !(e && e[0] == '0');
+    }();
+    if (five) {
+        static bool cfg5 = false;
+        if (!cfg5) {
+            cudaFuncSetAttribute(xy5_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(xy5_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cfg5 = true;
+        }
+        if (a.small_angle == 2)
+            xy5_kernel<2><<<grid, kX5NT, smem, st>>>(a, ntiles);
+        else
+            xy5_kernel<1><<<grid, kX5NT, smem, st>>>(a, ntiles);
+        return true;
+    }
     if (a.small_angle == 2)
         xy_pk_kernel<2><<<grid, kXpkNT, smem, st>>>(a, ntiles);
     else
