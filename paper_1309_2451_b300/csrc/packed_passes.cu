@@ -34,6 +34,11 @@
 // values, 64 registers); 512 threads cover a tile per phase, 16 warps per
 // SM.  The tile lives in the same ring of 128-row chunks as z_ring_kernel
 // and the next tile's copies are issued between phases.
+//
+// XY pass (xy_pk_kernel, complex64, nx = 256, 64-row tiles): three register
+// phases per direction (x = 16 x 16, y = 2 x 32) on 64 values per thread,
+// 256 threads; 10 passes of a tile through shared memory against the 14 of
+// the four-phase scalar passes (details at the kernel).
 #include <algorithm>
 #include <cstdlib>
 
@@ -228,9 +233,9 @@ template <int SITE, class L> __device__ __forceinline__ L tab_c(const L *t, long
 // taken from the plain index, the compiler keeps those values live from the
 // forward phase through every phase in between, which overflows the
 // 128-register budget of 512 threads into local memory.  The mirror phase
-// phases that close the longest such spans (B' and A' in the Z pass, P5 in
-// the XY pass, A' in the five-bit XY pass) take their index through this
-// move instead: no spills (ptxas -v).
+// phases that close the longest such spans (B' and A' in the Z pass, A' in
+// the XY pass) take their index through this move instead: no spills
+// (ptxas -v).
 __device__ __forceinline__ int phase_tid()
 {
     int t;
@@ -315,26 +320,33 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
             }
         }
     };
-    auto load_tabs = [&](int i) {
+    // per-tile tables: fetched from global memory into a register early in a
+    // phase and stored to shared memory at its end, so the global latency
+    // hides behind that phase's arithmetic (a direct global -> shared copy
+    // at the top of a tile held the whole CTA at the next barrier)
+    auto fetch_tabs = [&](int i) {
+        Lift<T> v{};
         if (t0 < C + P - 1) {
             const int t = t0;
             const int tile = blockIdx.x + i * G;
             const int tl = tile & ((1 << g.lgzt) - 1);
             const int kp = tl >> g.nblk_lg, b = tl & nblk_mask;
-            Lift<T> v;
             if (t < C) {
                 const int kx = b * W + (t & (W - 1)), ky = kp + ((t / W) << g.lgLy);
                 v = tab_c<3>(kxy, ((long long)ky << g.lgnx) + kx, (long long)g.nx * g.ny);
             } else {
                 v = a.tw[g.cross_off + (((t - C + 1) * kp) & (g.ny - 1))];
             }
-            tabs[i & 1][t0] = v;
         }
+        return v;
+    };
+    auto put_tabs = [&](int i, const Lift<T> &v) {
+        if (t0 < C + P - 1) tabs[i & 1][t0] = v;
     };
 
     if (nmine > 0) {
         issue(0, 0, NCH);
-        load_tabs(0);
+        put_tabs(0, fetch_tabs(0));
     }
     cp_async_commit();
     for (int e = t0; e < NZ; e += NT) {
@@ -351,7 +363,6 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
         const long long colbase = (long long)(tile >> g.lgzt) * g.rstride +
                                   ((long long)(kp * P) << g.lgnx) + b * W;
         const bool more = i + 1 < nmine;
-        if (more) load_tabs(i + 1);
         cp_async_wait_all();
         __syncthreads();                               // tile i and its tables visible
         const Lift<T> *tb = tabs[i & 1];
@@ -404,8 +415,9 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
         __syncthreads();
 
         // ---- B: radix-16 over b, then the twiddle of the last stage,
-        //      exp(-2 pi i c (k0 + 4 k1)/1024)
+        //      exp(-2 pi i c (k0 + 4 k1)/1024); the next tile's tables
         {
+            const Lift<T> ntab = more ? fetch_tabs(i + 1) : Lift<T>{};
             const int t = threadIdx.x;
             const int q = t & 7, c = (t >> 3) & 15, k0 = t >> 7;
             Q v[16];
@@ -422,6 +434,7 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
                 const int zz = 256 * k0 + 16 * k1 + c;
                 st_soa_c<8>(ring, piece(sl(zz / CHZ), zz, q), RINGE, w);
             }
+            if (more) put_tabs(i + 1, ntab);
         }
         if (more) issue(i + 1, 1, 2);
         __syncthreads();
@@ -539,20 +552,6 @@ __global__ void __launch_bounds__(kZpkNT, 1) z_pk_kernel(const ZArgs<float> a, i
     cp_async_wait_all();
 }
 
-// ============================================================== XY (packed)
-// Steady real-time XY pass (nx = 256, 64-row tiles, product potential,
-// merged half-kicks, in place), persistent with the ring of three 32-row
-// half buffers of xy_ring_kernel.  Stages as there: P1 inverse x last stage,
-// P2 inverse x first stage, P3a inverse y last stage, P3b inverse y first
-// stage + potential factor + forward y first stage, P3c forward y last
-// stage, P4 forward x first stage, P5 forward x last stage to HBM.
-//
-// Pairs: the x stages pair tile rows rw and rw + 32 (one in each half
-// buffer); between P1 and P2 and between P3c and P5 the tile is kept "split":
-// the real-part pair of a position in the first half buffer, the
-// imaginary-part pair in the second.  The y stages pair adjacent columns:
-// from P2 to P3c every 16-byte piece of a row holds (re_p, re_p+1, im_p,
-// im_p+1).  512 threads, 32 complex values (16 pairs) each per phase.
 namespace {
 
 // potential factor exp(-i th) as lifting pairs for |th| <= 0.16 (TIER 2:
@@ -579,293 +578,16 @@ template <int TIER> __device__ __forceinline__ void qkick_coef(float2 th, float2
     }
 }
 
-constexpr int kXpkNT = 512;
 
 }  // namespace
 
-template <int TIER>
-__global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a, int ntiles)
-{
-    constexpr int NX = 256, RA = 16, RB = 16, LY = 64, YA = 8, YB = 8, NT = kXpkNT;
-    constexpr int PITCH = NX + 2;                // complex values per row (16-byte rows)
-    constexpr int HR = LY / 2;                   // rows per half buffer
-    constexpr int HB = HR * PITCH;               // complex values per half buffer
-    constexpr int PPR = NX / 2;                  // 16-byte pieces per row
-    constexpr int RPI = NT / PPR;                // rows per copy round
-    constexpr int NCR = HR / RPI;                // copy rounds per half (8)
-    static_assert(NCR == 8 && RA * RB == NX && YA * YB == LY, "geometry");
-    using T = float;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *bufs = reinterpret_cast<float2 *>(smraw);
-    Lift<T> *wx = reinterpret_cast<Lift<T> *>(bufs + 3 * HB);   // [rr RA + j] = exp(-2 pi i j rr/NX)
-    Lift<T> *wy = wx + NX;                                      // exp(-2 pi i e/LY)
-    __shared__ T gtab[2][LY];                    // g(y) of the tile's rows, per tile
-    __shared__ float2 htab[2][NX / 2];           // H(x, z) tau at swapped positions (pairs)
-    __shared__ T thzs[2];                        // z-only phase, per tile
-
-    const Geom &g = a.g;
-    const Kick<T> &k = a.k;
-    const int t0 = threadIdx.x;
-    const int G = gridDim.x;
-    const int nmine = (ntiles - (int)blockIdx.x + G - 1) / G;
-    const T tau = k.tau_full;
-    constexpr int BUFE = 3 * HB;                       // float2 values in the half buffers
-    [[maybe_unused]] const long long NTOT = (long long)g.batch * g.rstride;
-    auto unswx = [](int q) { return q / RA + RB * (q % RA); };
-    auto half_buf = [&](int i, int h) { return bufs + ((2 * i + h) % 3) * HB; };
-    const int cpiece = t0 % PPR, crow = t0 / PPR;
-    auto issue = [&](int i, int h, int m0, int m1) {
-        const int tile = blockIdx.x + i * G;
-        const int z = tile >> g.lgP, r = tile & (g.P - 1);
-        long long so = (long long)z * g.plane + ((long long)((h * HR + crow + RPI * m0) * g.P + r) << g.lgnx) +
-                       2 * cpiece;
-        int d = (int)(half_buf(i, h) - bufs) + (crow + RPI * m0) * PITCH + 2 * cpiece;
-        const long long rstep = (long long)(RPI * g.P) << g.lgnx;
-        for (int m = m0; m < m1; ++m) {
-            if (CTAP_BOUNDS(21, d, BUFE - 1) && CTAP_BOUNDS(22, so, NTOT - 1))
-                cp_async16(bufs + d, a.src + so);
-            so += rstep;
-            d += RPI * PITCH;
-        }
-    };
-    auto load_tabs = [&](int i) {
-        const int tile = blockIdx.x + i * G;
-        const int z = tile >> g.lgP, r = tile & (g.P - 1);
-        if (t0 < LY) gtab[i & 1][t0] = k.g[r + t0 * g.P];
-        if (t0 < NX / 2) {
-            const long long hz = (long long)z * g.nx;
-            htab[i & 1][t0] = make_float2(k.H[hz + unswx(2 * t0)] * tau, k.H[hz + unswx(2 * t0 + 1)] * tau);
-        }
-        if (t0 == 0) thzs[i & 1] = k.vz ? k.vz[z & (g.nz - 1)] * tau : T(0);
-    };
-
-    if (nmine > 0) {
-        issue(0, 0, 0, NCR);
-        issue(0, 1, 0, NCR);
-        load_tabs(0);
-    }
-    cp_async_commit();
-    for (int e = t0; e < NX + LY; e += NT)
-        wx[e] = e < NX ? a.tw[g.fast_x_off + (e % RA) * (e / RA)] : a.tw[g.fast_y_off + e - NX];
-
-    for (int i = 0; i < nmine; ++i) {
-        const int tile = blockIdx.x + i * G;
-        const int z = tile >> g.lgP, r = tile & (g.P - 1);
-        const bool more = i + 1 < nmine;
-        if (more) load_tabs(i + 1);
-        cp_async_wait_all();
-        __syncthreads();                         // tile i (and its tables) visible
-        // offsets (float2 values) of the tile's two half buffers
-        const int o0 = (int)(half_buf(i, 0) - bufs), o1 = (int)(half_buf(i, 1) - bufs);
-
-        // P1: inverse x, last stage (radix RB), rows rw and rw + 32 as a pair;
-        //     AoS in, split out
-        {
-            const int t = threadIdx.x;
-            const int j = t & 15, rw = t >> 4;
-            const int pa = o0 + rw * PITCH + j, pb = o1 + rw * PITCH + j;
-            Q v[RB];
-#pragma unroll
-            for (int kk = 0; kk < RB; ++kk) {
-                const float2 ea = ld2_c<23>(bufs, pa + RA * kk, BUFE), eb = ld2_c<23>(bufs, pb + RA * kk, BUFE);
-                v[brev(kk, RB)] = Q{make_float2(ea.x, eb.x), make_float2(ea.y, eb.y)};
-            }
-            qdft_inv<RB, 0, 1>(v);
-#pragma unroll
-            for (int rr = 1; rr < RB; ++rr) qlift_b(v[rr], tab_c<24>(wx, rr * RA + j, NX));
-#pragma unroll
-            for (int rr = 0; rr < RB; ++rr) {
-                st2_c<25>(bufs, pa + RA * rr, BUFE, v[rr].x);
-                st2_c<25>(bufs, pb + RA * rr, BUFE, v[rr].y);
-            }
-        }
-        if (more) issue(i + 1, 0, 0, 2);
-        __syncthreads();
-
-        // P2: inverse x, first stage (radix RA) on 16 contiguous positions;
-        //     split in, column pairs out
-        {
-            const int t = threadIdx.x;
-            const int rw = t & 31, j = t >> 5;
-            const int pa = o0 + rw * PITCH + RA * j, pb = o1 + rw * PITCH + RA * j;
-            Q v[RA];
-#pragma unroll
-            for (int m = 0; m < RA; m += 2) {
-                const float4 xr = ld4_c<26>(bufs, pa + m, BUFE);
-                const float4 xi = ld4_c<26>(bufs, pb + m, BUFE);
-                v[brev(m, RA)] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
-                v[brev(m + 1, RA)] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
-            }
-            qdft_inv<RA, 0, 1>(v);
-#pragma unroll
-            for (int m = 0; m < RA; m += 2) {
-                st4_c<27>(bufs, pa + m, BUFE, make_float4(v[m].x.x, v[m + 1].x.x, v[m].y.x, v[m + 1].y.x));
-                st4_c<27>(bufs, pb + m, BUFE, make_float4(v[m].x.y, v[m + 1].x.y, v[m].y.y, v[m + 1].y.y));
-            }
-        }
-        if (more) issue(i + 1, 0, 2, 4);
-        __syncthreads();
-
-        // row ii + YA kk (kk < YB) of the tile, at column piece q (16 bytes)
-        auto yrow = [&](int row, int q) { return (row < HR ? o0 : o1) + (row % HR) * PITCH + 2 * q; };
-
-        // P3a: inverse y, last stage (radix YB) on rows ii + YA kk, two
-        //      column pairs (pieces pp and pp + 64)
-        {
-            const int t = threadIdx.x;
-            const int pp = t & 63, ii = t >> 6;
-            Q v[2][YB];
-#pragma unroll
-            for (int kk = 0; kk < YB; ++kk) {
-                v[0][brev(kk, YB)] = ld_soa_c<28>(bufs, yrow(ii + YA * kk, pp), BUFE);
-                v[1][brev(kk, YB)] = ld_soa_c<28>(bufs, yrow(ii + YA * kk, pp + 64), BUFE);
-            }
-            qdft_inv<YB, 0, 1>(v[0]);
-            qdft_inv<YB, 0, 1>(v[1]);
-#pragma unroll
-            for (int rr = 1; rr < YB; ++rr) {
-                const Lift<T> tw = tab_c<33>(wy, ii * rr, LY);
-                qlift_b(v[0][rr], tw);
-                qlift_b(v[1][rr], tw);
-            }
-#pragma unroll
-            for (int rr = 0; rr < YB; ++rr) {
-                st_soa_c<29>(bufs, yrow(ii + YA * rr, pp), BUFE, v[0][rr]);
-                st_soa_c<29>(bufs, yrow(ii + YA * rr, pp + 64), BUFE, v[1][rr]);
-            }
-        }
-        if (more) issue(i + 1, 0, 4, 6);
-        __syncthreads();
-
-        // P3b: inverse y first stage -> potential factor -> forward y first
-        //      stage on rows YA ii + kk (one half buffer)
-        {
-            const int t = threadIdx.x;
-            const int pp = t & 63, ii = t >> 6;
-            const T *gt = gtab[i & 1];
-            const T thz = thzs[i & 1];
-            Q v[2][YA];
-#pragma unroll
-            for (int kk = 0; kk < YA; ++kk) {
-                v[0][brev(kk, YA)] = ld_soa_c<30>(bufs, yrow(YA * ii + kk, pp), BUFE);
-                v[1][brev(kk, YA)] = ld_soa_c<30>(bufs, yrow(YA * ii + kk, pp + 64), BUFE);
-            }
-            qdft_inv<YA, 0, 1>(v[0]);
-            qdft_inv<YA, 0, 1>(v[1]);
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const float2 hx = htab[i & 1][pp + 64 * c];
-#pragma unroll
-                for (int rr = 0; rr < YA; ++rr) {
-                    // v[c][rr]: real-space row jy = ii + YB rr
-                    float2 p, u;
-                    qkick_coef<TIER>(fma2(pk(gt[ii + YB * rr]), hx, pk(thz)), p, u);
-                    qrot_f(v[c][rr], p, u);
-                }
-            }
-            qdft_fwd<YA, 0, 1>(v[0]);
-            qdft_fwd<YA, 0, 1>(v[1]);
-#pragma unroll
-            for (int kk = 0; kk < YA; ++kk) {
-                st_soa_c<31>(bufs, yrow(YA * ii + kk, pp), BUFE, v[0][brev(kk, YA)]);
-                st_soa_c<31>(bufs, yrow(YA * ii + kk, pp + 64), BUFE, v[1][brev(kk, YA)]);
-            }
-        }
-        if (more) issue(i + 1, 0, 6, 8);
-        cp_async_commit();
-        __syncthreads();
-
-        // P3c: forward y, last stage (radix YB) on rows ii + YA rr; column
-        //      pairs in, split out (rows ii + YA m and ii + YA m + 32 pair up)
-        {
-            const int t = threadIdx.x;
-            const int pp = t & 63, ii = t >> 6;
-            Q v[2][YB];
-#pragma unroll
-            for (int rr = 0; rr < YB; ++rr) {
-                v[0][rr] = ld_soa_c<32>(bufs, yrow(ii + YA * rr, pp), BUFE);
-                v[1][rr] = ld_soa_c<32>(bufs, yrow(ii + YA * rr, pp + 64), BUFE);
-            }
-#pragma unroll
-            for (int rr = 1; rr < YB; ++rr) {
-                const Lift<T> tw = tab_c<33>(wy, ii * rr, LY);
-                qlift_f(v[0][rr], tw);
-                qlift_f(v[1][rr], tw);
-            }
-            qdft_fwd<YB, 0, 1>(v[0]);
-            qdft_fwd<YB, 0, 1>(v[1]);
-            // output row ii + YA k2 sits in v[c][brev(k2)]; rows k2 and k2 + 4
-            // (local row ii + YA m of each half buffer) form a pair
-#pragma unroll
-            for (int mm = 0; mm < YB / 2; ++mm) {
-                const int lr = ii + YA * mm;
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const Q &qa = v[c][brev(mm, YB)], &qb = v[c][brev(mm + YB / 2, YB)];
-                    const int off = lr * PITCH + 2 * (pp + 64 * c);
-                    st4_c<34>(bufs, o0 + off, BUFE, make_float4(qa.x.x, qb.x.x, qa.x.y, qb.x.y));
-                    st4_c<34>(bufs, o1 + off, BUFE, make_float4(qa.y.x, qb.y.x, qa.y.y, qb.y.y));
-                }
-            }
-        }
-        __syncthreads();
-
-        // P4: forward x, first stage (radix RA) on 16 contiguous positions, split
-        {
-            const int t = threadIdx.x;
-            const int rw = t & 31, j = t >> 5;
-            const int pa = o0 + rw * PITCH + RA * j, pb = o1 + rw * PITCH + RA * j;
-            Q v[RA];
-#pragma unroll
-            for (int m = 0; m < RA; m += 2) {
-                const float4 xr = ld4_c<35>(bufs, pa + m, BUFE);
-                const float4 xi = ld4_c<35>(bufs, pb + m, BUFE);
-                v[m] = Q{make_float2(xr.x, xr.y), make_float2(xi.x, xi.y)};
-                v[m + 1] = Q{make_float2(xr.z, xr.w), make_float2(xi.z, xi.w)};
-            }
-            qdft_fwd<RA, 0, 1>(v);
-#pragma unroll
-            for (int m = 0; m < RA; m += 2) {
-                const Q &e0 = v[brev(m, RA)], &e1 = v[brev(m + 1, RA)];
-                st4_c<36>(bufs, pa + m, BUFE, make_float4(e0.x.x, e0.x.y, e1.x.x, e1.x.y));
-                st4_c<36>(bufs, pb + m, BUFE, make_float4(e0.y.x, e0.y.y, e1.y.x, e1.y.y));
-            }
-        }
-        __syncthreads();
-
-        // P5: forward x, last stage, to HBM.  The task is read back first so
-        //     that both half buffers can take the next tile's second half.
-        {
-            const int t = phase_tid();
-            const int j = t & 15, rw = t >> 4;
-            Q v[RB];
-#pragma unroll
-            for (int rr = 0; rr < RB; ++rr)
-                v[rr] = Q{ld2_c<37>(bufs, o0 + rw * PITCH + j + RA * rr, BUFE),
-                          ld2_c<37>(bufs, o1 + rw * PITCH + j + RA * rr, BUFE)};
-            __syncthreads();                     // tile i's buffers are free
-            if (more) issue(i + 1, 1, 0, NCR);
-            cp_async_commit();
-#pragma unroll
-            for (int rr = 1; rr < RB; ++rr) qlift_f(v[rr], tab_c<24>(wx, rr * RA + j, NX));
-            qdft_fwd<RB, 0, 1>(v);
-            const long long oa = (long long)z * g.plane + ((long long)(rw * g.P + r) << g.lgnx) + j;
-            const long long ob = oa + ((long long)(HR * g.P) << g.lgnx);
-#pragma unroll
-            for (int k2 = 0; k2 < RB; ++k2) {
-                const Q &e = v[brev(k2, RB)];
-                if (CTAP_BOUNDS(38, oa + RA * k2, NTOT)) a.dst[oa + RA * k2] = make_float2(e.x.x, e.y.x);
-                if (CTAP_BOUNDS(38, ob + RA * k2, NTOT)) a.dst[ob + RA * k2] = make_float2(e.x.y, e.y.y);
-            }
-        }
-    }
-    cp_async_wait_all();
-}
-
-// ======================================================== XY (packed, 5-bit)
-// The same steady XY pass in three register phases per direction instead of
-// four, so a tile passes through shared memory 10 times instead of 14:
-//   x = 16 x1 + x2, kx = k1 + 16 k2 (as xy_pk_kernel); y = 2 j1 + j2 (j1 < 32),
+// ============================================================== XY (packed)
+// Steady real-time XY pass (nx = 256, 64-row tiles, product potential,
+// merged half-kicks, in place), persistent with the ring of three 32-row
+// half buffers of xy_ring_kernel, in three register phases per direction
+// (the scalar passes take four), so a tile passes through shared memory 10
+// times instead of 14:
+//   x = 16 x1 + x2, kx = k1 + 16 k2 (as xy_ring_kernel); y = 2 j1 + j2 (j1 < 32),
 //   k' = k1 + 32 k2 (k2 < 2)
 //   A   inverse x, last stage (radix 16 over k2 for fixed k1, from the ring,
 //       rows rw and rw + 32 paired), inverse twiddle exp(2 pi i x2 k1/256);
@@ -880,12 +602,12 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
 // C and B' pair positions p and p + 128 of one row, kept "split" in shared
 // memory: the pair of real parts at position p, the pair of imaginary parts
 // at position p + 128.
-constexpr int kX5NT = 256;
+constexpr int kXpkNT = 256;
 
 template <int TIER>
-__global__ void __launch_bounds__(kX5NT, 1) xy5_kernel(const XYArgs<float> a, int ntiles)
+__global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a, int ntiles)
 {
-    constexpr int NX = 256, LY = 64, NT = kX5NT;
+    constexpr int NX = 256, LY = 64, NT = kXpkNT;
     constexpr int PITCH = NX + 2;                // complex values per row (16-byte rows)
     constexpr int HR = LY / 2;                   // rows per half buffer
     constexpr int HB = HR * PITCH;               // complex values per half buffer
@@ -926,21 +648,33 @@ __global__ void __launch_bounds__(kX5NT, 1) xy5_kernel(const XYArgs<float> a, in
             d += RPI * PITCH;
         }
     };
-    auto load_tabs = [&](int i) {
+    // per-tile tables (g of the rows, H tau of the column pairs, the z-only
+    // phase): fetched into registers early in phase B and stored to shared
+    // memory at its end (the global latency hides behind B's arithmetic)
+    struct Tabs { float h0, h1, gy, vz; };
+    auto fetch_tabs = [&](int i) {
+        Tabs v{0.0f, 0.0f, 0.0f, 0.0f};
         const int tile = blockIdx.x + i * G;
         const int z = tile >> g.lgP, r = tile & (g.P - 1);
-        if (t0 < LY) gtab[i & 1][t0] = k.g[r + t0 * g.P];
+        if (t0 < LY) v.gy = k.g[r + t0 * g.P];
         if (t0 < NX / 2) {
             const long long hz = (long long)z * g.nx;
-            htab[i & 1][t0] = make_float2(k.H[hz + unswx(t0)] * tau, k.H[hz + unswx(t0 + NX / 2)] * tau);
+            v.h0 = k.H[hz + unswx(t0)] * tau;
+            v.h1 = k.H[hz + unswx(t0 + NX / 2)] * tau;
         }
-        if (t0 == 0) thzs[i & 1] = k.vz ? k.vz[z & (g.nz - 1)] * tau : T(0);
+        if (t0 == 0) v.vz = k.vz ? k.vz[z & (g.nz - 1)] * tau : T(0);
+        return v;
+    };
+    auto put_tabs = [&](int i, const Tabs &v) {
+        if (t0 < LY) gtab[i & 1][t0] = v.gy;
+        if (t0 < NX / 2) htab[i & 1][t0] = make_float2(v.h0, v.h1);
+        if (t0 == 0) thzs[i & 1] = v.vz;
     };
 
     if (nmine > 0) {
         issue(0, 0, 0, NCR);
         issue(0, 1, 0, NCR);
-        load_tabs(0);
+        put_tabs(0, fetch_tabs(0));
     }
     cp_async_commit();
     for (int e = t0; e < NX + LY; e += NT)
@@ -950,7 +684,6 @@ __global__ void __launch_bounds__(kX5NT, 1) xy5_kernel(const XYArgs<float> a, in
         const int tile = blockIdx.x + i * G;
         const int z = tile >> g.lgP, r = tile & (g.P - 1);
         const bool more = i + 1 < nmine;
-        if (more) load_tabs(i + 1);
         cp_async_wait_all();
         __syncthreads();
         const int o0 = half_buf(i, 0), o1 = half_buf(i, 1);
@@ -984,8 +717,10 @@ __global__ void __launch_bounds__(kX5NT, 1) xy5_kernel(const XYArgs<float> a, in
         __syncthreads();
 
         // B: inverse x first stage (16 contiguous positions of x2 and of
-        //    x2 + 8) and inverse y last stage (rows k1, k1 + 32), in place
+        //    x2 + 8) and inverse y last stage (rows k1, k1 + 32), in place;
+        //    the next tile's tables
         {
+            const Tabs ntab = more ? fetch_tabs(i + 1) : Tabs{0.0f, 0.0f, 0.0f, 0.0f};
             const int t = threadIdx.x;
             const int k1 = t & 31, x2 = t >> 5;
             const int ra = o0 + k1 * PITCH + 16 * x2, rb = o1 + k1 * PITCH + 16 * x2;
@@ -1020,6 +755,7 @@ __global__ void __launch_bounds__(kX5NT, 1) xy5_kernel(const XYArgs<float> a, in
                     st4_c<48>(bufs, ro + m + 128, BUFE, make_float4(v[h][m].y.x, v[h][m].y.y, v[h][m + 1].y.x, v[h][m + 1].y.y));
                 }
             }
+            if (more) put_tabs(i + 1, ntab);
         }
         if (more) issue(i + 1, 0, 4, 8);
         __syncthreads();
@@ -1172,24 +908,6 @@ bool launch_xy_packed(const XYArgs<float> &a, cudaStream_t st)
     }
     const int ntiles = xy_grid(a.g);
     const int grid = std::min(ntiles, pk_sm_count());
-    // the five-bit pass by default; CTAP_XY5=0 keeps the four-bit pass
-    static const bool five = [] {
-        const char *e = std::getenv("CTAP_XY5");
-        return !(e && e[0] == '0');
-    }();
-    if (five) {
-        static bool cfg5 = false;
-        if (!cfg5) {
-            cudaFuncSetAttribute(xy5_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(xy5_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cfg5 = true;
-        }
-        if (a.small_angle == 2)
-            xy5_kernel<2><<<grid, kX5NT, smem, st>>>(a, ntiles);
-        else
-            xy5_kernel<1><<<grid, kX5NT, smem, st>>>(a, ntiles);
-        return true;
-    }
     if (a.small_angle == 2)
         xy_pk_kernel<2><<<grid, kXpkNT, smem, st>>>(a, ntiles);
     else
