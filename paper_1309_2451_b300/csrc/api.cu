@@ -715,6 +715,25 @@ void clear_potential(PlanState &st)
     invalidate_sep(st);
 }
 
+// max over the grid of |Vx(x) + Vy(y) + Vz(z)|: the sum is extreme where
+// every axis term is (the largest or the smallest of each)
+double separable_vmax(const PlanState &st)
+{
+    double hi = 0.0, lo = 0.0;
+    size_t o = 0;
+    for (int n : {st.nx, st.ny, st.nz}) {
+        double mx = st.h_vsep[o], mn = st.h_vsep[o];
+        for (int i = 1; i < n; ++i) {
+            mx = std::max(mx, st.h_vsep[o + i]);
+            mn = std::min(mn, st.h_vsep[o + i]);
+        }
+        hi += mx;
+        lo += mn;
+        o += n;
+    }
+    return std::max(std::fabs(hi), std::fabs(lo));
+}
+
 ctap_status set_product(PlanState &st, const std::vector<double> &gy, const std::vector<double> &H)
 {
     clear_potential(st);
@@ -1003,6 +1022,7 @@ ctap_status ctap_set_potential_separable(ctap_plan_t plan, const double *Vx, con
         if (!std::isfinite(v)) return fail(*st, CTAP_ERR_INVALID_ARG, "non-finite potential");
     CTAP_TRY(upload64(*st, &st->d_vsep64, st->h_vsep));
     st->vform = VF_SEPARABLE;
+    st->vmax = separable_vmax(*st);
     st->have_guides = false;
     st->have_spline = false;
     invalidate_sep(*st);
@@ -1103,6 +1123,7 @@ ctap_status ctap_add_potential_z(ctap_plan_t plan, const double *Vz)
     } else if (st->vform == VF_SEPARABLE) {
         for (int z = 0; z < nz; ++z) st->h_vsep[(size_t)nx + ny + z] += Vz[z];
         CTAP_TRY(upload64(*st, &st->d_vsep64, st->h_vsep));
+        st->vmax = separable_vmax(*st);
         invalidate_sep(*st);
     } else {
         if (st->h_vz.empty()) st->h_vz.assign(nz, 0.0);
@@ -1293,9 +1314,13 @@ ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5])
     info[3] = st->N * st->esize;
     const bool ring = st->fast_z && !st->no_ring && st->dtype == CTAP_C64 && st->nz == 1024 &&
                       st->geom.P == 4 && st->geom.w == 4;
-    const bool xy_ring = st->fast_xy && !st->no_ring && st->dtype == CTAP_C64 && st->nx == 256 &&
-                         st->geom.Ly == 64;
-    const bool xy_packed = xy_ring && !st->no_packed && packed_xy_supported(st->geom);
+    // the steady XY ring passes take the product form; the packed one also
+    // the separable form
+    const bool xy_ring_geom = st->fast_xy && !st->no_ring && st->dtype == CTAP_C64 && st->nx == 256 &&
+                              st->geom.Ly == 64;
+    const bool xy_packed = xy_ring_geom && !st->no_packed && packed_xy_supported(st->geom) &&
+                           (st->vform == VF_PRODUCT || st->vform == VF_SEPARABLE);
+    const bool xy_ring = xy_ring_geom && (st->vform == VF_PRODUCT || xy_packed);
     info[4] = (st->fast_xy ? 1 : 0) | (st->fast_z ? 2 : 0) | (ring ? 4 : 0) | (xy_ring ? 8 : 0) |
               (packed_z_on(*st) ? 16 : 0) | (xy_packed ? 32 : 0);
     return CTAP_OK;

@@ -582,8 +582,8 @@ template <int TIER> __device__ __forceinline__ void qkick_coef(float2 th, float2
 }  // namespace
 
 // ============================================================== XY (packed)
-// Steady real-time XY pass (nx = 256, 64-row tiles, product potential,
-// merged half-kicks, in place), persistent with the ring of three 32-row
+// Steady real-time XY pass (nx = 256, 64-row tiles, product or separable
+// potential, merged half-kicks, in place), persistent with the ring of three 32-row
 // half buffers of xy_ring_kernel, in three register phases per direction
 // (the scalar passes take four), so a tile passes through shared memory 10
 // times instead of 14:
@@ -604,7 +604,7 @@ template <int TIER> __device__ __forceinline__ void qkick_coef(float2 th, float2
 // at position p + 128.
 constexpr int kXpkNT = 256;
 
-template <int TIER>
+template <int TIER, bool SEP>
 __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a, int ntiles)
 {
     constexpr int NX = 256, LY = 64, NT = kXpkNT;
@@ -619,9 +619,11 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
     float2 *bufs = reinterpret_cast<float2 *>(smraw);
     Lift<T> *wx = reinterpret_cast<Lift<T> *>(bufs + 3 * HB);   // [x2 16 + k1] = exp(-2 pi i k1 x2/256)
     Lift<T> *wy = wx + NX;                                      // exp(-2 pi i e/64)
-    __shared__ T gtab[2][LY];                    // g(y), y = r + P j, per tile
-    __shared__ float2 htab[2][NX / 2];           // H(x(p), z) tau and H(x(p + 128), z) tau
-    __shared__ T thzs[2];
+    // angle of the kick at (x, y) of the tile's plane z: g(y) h(x) + thz
+    // (product form) or h(x) + g(y) (separable form)
+    __shared__ T gtab[2][LY];                    // product: g(y); separable: (Vy(y) + Vz(z)) tau
+    __shared__ float2 htab[2][NX / 2];           // product: H(x, z) tau; separable: Vx(x) tau
+    __shared__ T thzs[2];                        // product: Vz(z) tau
 
     const Geom &g = a.g;
     const Kick<T> &k = a.k;
@@ -648,21 +650,36 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
             d += RPI * PITCH;
         }
     };
-    // per-tile tables (g of the rows, H tau of the column pairs, the z-only
-    // phase): fetched into registers early in phase B and stored to shared
-    // memory at its end (the global latency hides behind B's arithmetic)
+    // per-tile tables (the row and column factors of the kick angle, the
+    // z-only phase): fetched into registers early in phase B and stored to
+    // shared memory at its end (the global latency hides behind B's
+    // arithmetic).  Separable form: the angles are formed from the FP64 axis
+    // potentials and rounded once.
     struct Tabs { float h0, h1, gy, vz; };
     auto fetch_tabs = [&](int i) {
         Tabs v{0.0f, 0.0f, 0.0f, 0.0f};
         const int tile = blockIdx.x + i * G;
         const int z = tile >> g.lgP, r = tile & (g.P - 1);
-        if (t0 < LY) v.gy = k.g[r + t0 * g.P];
-        if (t0 < NX / 2) {
-            const long long hz = (long long)z * g.nx;
-            v.h0 = k.H[hz + unswx(t0)] * tau;
-            v.h1 = k.H[hz + unswx(t0 + NX / 2)] * tau;
+        if constexpr (SEP) {
+            const double *Vs = a.rd.Vsep;              // [nx | ny | nz]
+            const long long nv = (long long)g.nx + g.ny + g.nz;
+            const double td = (double)tau;
+            if (t0 < LY)
+                v.gy = (float)((tab_c<57>(Vs, g.nx + r + t0 * g.P, nv) +
+                                tab_c<57>(Vs, g.nx + g.ny + (z & (g.nz - 1)), nv)) * td);
+            if (t0 < NX / 2) {
+                v.h0 = (float)(tab_c<58>(Vs, unswx(t0), nv) * td);
+                v.h1 = (float)(tab_c<58>(Vs, unswx(t0 + NX / 2), nv) * td);
+            }
+        } else {
+            if (t0 < LY) v.gy = tab_c<59>(k.g, r + t0 * g.P, g.ny);
+            if (t0 < NX / 2) {
+                const long long hz = (long long)z * g.nx, nh = (long long)g.batch * g.nz * g.nx;   // [batch][nz][nx]
+                v.h0 = tab_c<60>(k.H, hz + unswx(t0), nh) * tau;
+                v.h1 = tab_c<60>(k.H, hz + unswx(t0 + NX / 2), nh) * tau;
+            }
+            if (t0 == 0) v.vz = k.vz ? tab_c<61>(k.vz, z & (g.nz - 1), g.nz) * tau : T(0);
         }
-        if (t0 == 0) v.vz = k.vz ? k.vz[z & (g.nz - 1)] * tau : T(0);
         return v;
     };
     auto put_tabs = [&](int i, const Tabs &v) {
@@ -777,7 +794,10 @@ __global__ void __launch_bounds__(kXpkNT, 1) xy_pk_kernel(const XYArgs<float> a,
 #pragma unroll
             for (int j1 = 0; j1 < 32; ++j1) {
                 float2 p, u;
-                qkick_coef<TIER>(fma2(pk(gt[2 * j1 + j2]), hx, pk(thz)), p, u);
+                if constexpr (SEP)
+                    qkick_coef<TIER>(add2(pk(gt[2 * j1 + j2]), hx), p, u);
+                else
+                    qkick_coef<TIER>(fma2(pk(gt[2 * j1 + j2]), hx, pk(thz)), p, u);
                 qrot_f(v[j1], p, u);
             }
             qdft_fwd<32, 0, 1>(v);
@@ -895,23 +915,30 @@ bool packed_xy_supported(const Geom &g)
 
 bool launch_xy_packed(const XYArgs<float> &a, cudaStream_t st)
 {
+    const bool sep = a.k.form == VF_SEPARABLE && a.rd.Vsep;
     const bool hot = a.flags == (XY_IN_MIXED | XY_OUT_MIXED | XY_KICK_FULL) &&
-                     a.k.form == VF_PRODUCT && !a.k.imag && a.small_angle >= 1;
+                     (a.k.form == VF_PRODUCT || sep) && !a.k.imag && a.small_angle >= 1;
     if (!hot || !a.ring || a.src != a.dst || !packed_xy_supported(a.g)) return false;
     constexpr int HB = 32 * 258;
     constexpr size_t smem = 3 * HB * sizeof(float2) + (256 + 64) * sizeof(Lift<float>);
     static bool cfg = false;
     if (!cfg) {
-        cudaFuncSetAttribute(xy_pk_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(xy_pk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(xy_pk_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(xy_pk_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(xy_pk_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(xy_pk_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cfg = true;
     }
     const int ntiles = xy_grid(a.g);
     const int grid = std::min(ntiles, pk_sm_count());
-    if (a.small_angle == 2)
-        xy_pk_kernel<2><<<grid, kXpkNT, smem, st>>>(a, ntiles);
+    if (sep && a.small_angle == 2)
+        xy_pk_kernel<2, true><<<grid, kXpkNT, smem, st>>>(a, ntiles);
+    else if (sep)
+        xy_pk_kernel<1, true><<<grid, kXpkNT, smem, st>>>(a, ntiles);
+    else if (a.small_angle == 2)
+        xy_pk_kernel<2, false><<<grid, kXpkNT, smem, st>>>(a, ntiles);
     else
-        xy_pk_kernel<1><<<grid, kXpkNT, smem, st>>>(a, ntiles);
+        xy_pk_kernel<1, false><<<grid, kXpkNT, smem, st>>>(a, ntiles);
     return true;
 }
 

@@ -1,8 +1,9 @@
 """The bounds-checked build (libctap_debug.so, -DCTAP_DEBUG_BOUNDS): every
 shared-memory and HBM index of the packed persistent passes is checked
 before the access, a violation is recorded and the access skipped (nothing
-traps).  Steps through both packed passes run in a child process on the
-checked library: no violation may be recorded, and the result must equal
+traps).  Steps through both packed passes (guide potential; the XY pass
+also with the separable oscillator) run in a child process on the checked
+library: no violation may be recorded, and the result must equal
 the normal library's (the checks change no arithmetic)."""
 import json
 import os
@@ -24,17 +25,22 @@ import numpy as np, torch
 sys.path.insert(0, sys.argv[1])
 from paper_1309_2451_b300 import ctap, workloads as wl
 out = {}
-for shape in ((64, 256, 256), (1024, 256, 64), (1024, 256, 256)):
-    box = wl.CTAP_BOX
-    c = wl.guide_centres(wl.axis(shape[0], box[4], box[5]))
-    plan = ctap.Plan(shape, box, "c64")
-    plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
-    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=31) \
+cases = [(s, "guides") for s in ((64, 256, 256), (1024, 256, 64), (1024, 256, 256))]
+for shape, pot in cases + [((64, 256, 256), "harmonic")]:
+    plan = ctap.Plan(shape, wl.CTAP_BOX if pot == "guides" else wl.HARMONIC_BOX, "c64")
+    if pot == "guides":
+        box = wl.CTAP_BOX
+        c = wl.guide_centres(wl.axis(shape[0], box[4], box[5]))
+        plan.set_guides(wl.V0, wl.SIGMA_GUIDE, c[0], c[2], wl.POP_HALFWIDTH)
+    else:
+        box = wl.HARMONIC_BOX
+        plan.set_potential_separable(*wl.harmonic_parts(shape, box))
+    psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -6, 6), seed=31) \
         * np.exp(2j * wl.mesh(shape, box)[2])
     psi = torch.from_numpy(psi0).to("cuda", torch.complex64)
     plan.step(psi, 4, 0.0025)
     plan.sync()
-    out[str(shape)] = {"mask": plan.info()["fast_mask"], "bounds": ctap.debug_bounds(),
+    out[str(shape) + pot] = {"mask": plan.info()["fast_mask"], "bounds": ctap.debug_bounds(),
                        "sum": psi.abs().double().sum().item(),
                        "l2": torch.linalg.vector_norm(psi.to(torch.complex128)).item(),
                        "first": [psi.flatten()[1234567 % psi.numel()].real.item()]}

@@ -439,6 +439,36 @@ def test_persistent_xy_ring_matches_plain_pass_and_oracle(ctap, monkeypatch):
         assert rel(v, ref) < 1e-6
 
 
+@pytest.mark.parametrize("dt", [0.005, 0.001])
+def test_separable_potential_on_packed_xy_pass(ctap, monkeypatch, dt):
+    """The harmonic oscillator (separable potential, Sec. IV's test case) on
+    256-wide planes with 64-row tiles runs its steady XY passes in the packed
+    ring kernel, with the kick angle (Vx + Vy + Vz) dt formed per point from
+    the FP64 axis potentials.  The scalar passes (CTAP_NO_PACKED=1) apply
+    three table rotations per point instead.  On [-8, 8]^3, |V|max dt is 0.48
+    at dt = 0.005 (the long kick series) and 0.096 at dt = 0.001 (the short
+    one).  Both must agree with each other and with the oracle after 4 steps."""
+    shape, box = (64, 256, 256), wl.HARMONIC_BOX
+    x, y, _ = wl.mesh(shape, box)
+    psi0 = wl.gaussian_sum(shape, box, seed=23) * np.exp(1j * (1.5 * x + y))
+    got = {}
+    for env, bits in ((None, 40), ("CTAP_NO_PACKED", 0)):
+        if env:
+            monkeypatch.setenv(env, "1")
+        plan, V = harmonic_plan(ctap, shape, box, "c64")
+        assert plan.info()["fast_mask"] & 40 == bits, plan.info()
+        psi = to_dev(psi0, "c64")
+        plan.step(psi, 4, dt)
+        got[env] = psi.cpu().numpy().astype(complex)
+        plan.close()
+        if env:
+            monkeypatch.delenv(env)
+    ref = oracle.step(psi0, V, box, dt, 4)
+    assert rel(got[None], got["CTAP_NO_PACKED"]) < 1e-6
+    for v in got.values():
+        assert rel(v, ref) < 1e-6
+
+
 def test_ring_with_16_byte_aligned_psi(ctap):
     """The persistent Z pass moves 16-byte pieces: a psi view that is 16- but
     not 32-byte aligned (row segments then straddle 32-byte sectors) gives
