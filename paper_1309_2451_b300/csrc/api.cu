@@ -898,9 +898,9 @@ ctap_status ctap_plan_create_batched(int nx, int ny, int nz, int batch, const do
         delete p;
         return CTAP_ERR_UNSUPPORTED_SIZE;
     }
-    if (dtype == CTAP_C128_DF) {          // double-float: specialised XY pass for nx = 256 only
-        st.fast_xy = st.fast_xy && nx == 256;
-        st.fast_z = false;
+    if (dtype == CTAP_C128_DF) {          // double-float: specialised XY pass for nx = 256,
+        st.fast_xy = st.fast_xy && nx == 256;   // specialised Z pass for nz = 1024
+        st.fast_z = st.fast_z && nz == 1024;
     }
     auto bail = [&](ctap_status s) {
         ctap_plan_destroy(p);

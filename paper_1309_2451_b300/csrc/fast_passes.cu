@@ -259,9 +259,13 @@ template <int NQ, int NT = kFastNT> __device__ void block_sum(double (&acc)[NQ],
 // threads per XY CTA (register budget): the hot complex64 variant fits in 64
 // registers and runs 1024 threads (32 warps hide more shared-memory and
 // HBM latency); the other complex64 variants 512, complex128 256
+// threads per XY CTA: complex64 512 (1024 for the hot steady variant, which
+// fits 64 registers), complex128 256 (255 registers), double-float 512 (its
+// arithmetic is chains of dependent FP32 operations: warps matter more than
+// registers, and one task per thread fits 128)
 template <class T, bool HOT = false> __host__ __device__ constexpr int xy_threads()
 {
-    return sizeof(T) == 4 ? (HOT ? 1024 : 512) : 256;
+    return sizeof(T) == 4 ? (HOT ? 1024 : 512) : (std::is_same<T, df>::value ? 512 : 256);
 }
 
 template <class T, int NX, int RA, int RB, int LY, int YA, int YB, bool IN_MIXED, bool OUT_MIXED,
@@ -1611,13 +1615,18 @@ bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st)
 }
 
 // Double-float: the specialised XY pass for 256-point rows (16-point
-// register DFTs); the Z pass runs on the generic kernel (fully unrolled
-// 32-point register DFTs in double-float arithmetic are too large to compile).
+// register DFTs) and the three-stage Z pass of z3_df_pass.cuh for
+// 1024-point z-lines (fully unrolled 32-point register DFTs in double-float
+// arithmetic are too large to compile); other z lengths and the
+// observables pass take the generic Z pass.
 bool launch_xy_fast(const XYArgs<df> &a, cudaStream_t st)
 {
     return try_xy<df, 256, 16, 16, 32, 4, 8>(a, st);
 }
-bool launch_z_fast(const ZArgs<df> &, cudaStream_t) { return false; }
+bool launch_z_fast(const ZArgs<df> &a, cudaStream_t st)
+{
+    return launch_z3_df_p8(a, st) || launch_z3_df_p4(a, st) || launch_z3_df_p2(a, st);
+}
 
 bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st)
 {

@@ -162,6 +162,11 @@ bool launch_xy_fast(const XYArgs<df> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<double> &a, cudaStream_t st);
 bool launch_z_fast(const ZArgs<df> &a, cudaStream_t st);
+// the double-float three-stage Z pass (z3_df_pass.cuh), one per tile
+// geometry: 8, 4 or 2 row classes x 1, 2 or 4 columns (false: not this one)
+bool launch_z3_df_p8(const ZArgs<df> &a, cudaStream_t st);
+bool launch_z3_df_p4(const ZArgs<df> &a, cudaStream_t st);
+bool launch_z3_df_p2(const ZArgs<df> &a, cudaStream_t st);
 
 // V = vs |B| - voff on the grid ([nz][ny][nx], FP64, device) from thin
 // current segments seg[7 m ..] = (A, C, I) and a uniform field bias

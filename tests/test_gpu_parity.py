@@ -598,6 +598,7 @@ def test_full_size_fp64_paths_match_oracle(ctap, dtype):
     parity bound."""
     shape, box = (1024, 256, 256), wl.CTAP_BOX
     plan, V, c = guides_plan(ctap, shape, box, dtype)
+    assert plan.info()["fast_mask"] & 3 == 3, plan.info()     # specialised XY and Z passes
     psi0 = wl.gaussian_sum(shape, (-6, 6, -6, 6, -40, 40), seed=12) \
         * np.exp(2j * wl.mesh(shape, box)[2])
     psi = to_dev(psi0, "c128")

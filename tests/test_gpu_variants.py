@@ -288,6 +288,35 @@ def test_double_float_guides_and_observables(ctap, order):
     assert np.allclose(got, want, rtol=1e-11, atol=1e-14)
 
 
+# (nz, ny, nx), row classes, steps: 1024-point z-lines on 256-wide planes take
+# the three-stage double-float Z pass, here with 4 and 2 row classes per Z
+# tile (2 and 4 columns); the 8-class geometry is the full 256x256x1024 size
+# (tests/test_gpu_parity.py::test_full_size_fp64_paths_match_oracle)
+DF_Z3_CASES = [((1024, 128, 256), 4, 3), ((1024, 64, 256), 2, 40)]
+
+
+@pytest.mark.parametrize("shape,row_classes,steps", DF_Z3_CASES)
+def test_double_float_three_stage_z_pass(ctap, shape, row_classes, steps):
+    """The double-float Z pass for 1024-point z-lines (16 x 4 x 16 register
+    stages) in each of its tile geometries: guides with the longitudinal
+    trap, moving packets, against the oracle at the complex128 target; the
+    observables (their kinetic sum takes the generic Z pass) against the
+    oracle's."""
+    box = wl.CTAP_BOX
+    plan, V, c = guides(ctap, shape, box, "c128df", trap=wl.TRAP_OMEGA)
+    info = plan.info()
+    assert info["fast_mask"] & 2 and info["row_classes"] == row_classes and \
+        info["cols_per_z_tile"] == 8, info
+    psi0 = guide_state(shape, box, 43)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, steps, 0.0025)
+    ref = oracle.step(psi0, V, box, 0.0025, steps)
+    assert rel(psi.cpu().numpy(), ref) < 1e-12
+    got = plan.observables(psi)
+    want = oracle.observables(ref, V, box, c, wl.POP_HALFWIDTH)
+    assert np.allclose(got, want, rtol=1e-11, atol=1e-14)
+
+
 def test_double_float_imaginary_time(ctap):
     shape, box = (32, 32, 32), (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
     vx, vy, vz = wl.harmonic_parts(shape, box)
