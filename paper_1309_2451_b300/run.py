@@ -24,7 +24,7 @@ import numpy as np
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--grid", type=int, nargs=3, default=[128, 128, 256])
-    p.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    p.add_argument("--dtype", choices=["c64", "c128", "c128df"], default="c64")
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--every", type=int, default=50)
     p.add_argument("--dt", type=float, default=0.005)
