@@ -233,7 +233,9 @@ ctap_status ctap_pass_times(ctap_plan_t plan, long long counts[3], double ms[3])
  * 16: the real-time Z ring runs in packed FP32-pair arithmetic, 32: the
  * steady XY ring runs in packed FP32-pair arithmetic).  Bits 8 and 32 depend
  * on the potential set: the scalar XY ring takes the product form, the
- * packed one the product and the separable forms.  CTAP_NO_PACKED=1 in
+ * packed one the product and the separable forms; both also need a time
+ * step with |V|max dt <= 0.5 (a larger kick angle takes the one-tile-per-CTA
+ * pass with the general kick).  CTAP_NO_PACKED=1 in
  * the environment at plan creation keeps the scalar ring kernels,
  * CTAP_NO_RING=1 the one-tile-per-CTA passes. */
 ctap_status ctap_plan_info(ctap_plan_t plan, long long info[5]);

@@ -469,6 +469,24 @@ def test_separable_potential_on_packed_xy_pass(ctap, monkeypatch, dt):
         assert rel(v, ref) < 1e-6
 
 
+def test_separable_packed_xy_with_trap_term(ctap):
+    """The separable oscillator plus an additive z-only term (the longitudinal
+    trap form, Sec. III) on the packed XY pass: the term folds into the z
+    axis potential, and |V|max for the series tier includes it."""
+    shape, box = (64, 256, 256), wl.HARMONIC_BOX
+    z = wl.axis(shape[0], box[4], box[5])
+    extra = 0.5 * np.sin(0.7 * z)
+    plan, V = harmonic_plan(ctap, shape, box, "c64")
+    plan.add_potential_z(extra)
+    V = V + extra[:, None, None]
+    assert plan.info()["fast_mask"] & 40 == 40, plan.info()
+    x, y, _ = wl.mesh(shape, box)
+    psi0 = wl.gaussian_sum(shape, box, seed=24) * np.exp(1j * (x - 2.0 * y))
+    psi = to_dev(psi0, "c64")
+    plan.step(psi, 4, 0.005)
+    assert rel(psi.cpu().numpy().astype(complex), oracle.step(psi0, V, box, 0.005, 4)) < 1e-6
+
+
 def test_ring_with_16_byte_aligned_psi(ctap):
     """The persistent Z pass moves 16-byte pieces: a psi view that is 16- but
     not 32-byte aligned (row segments then straddle 32-byte sectors) gives
