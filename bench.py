@@ -574,9 +574,11 @@ def time_sweep(ctap, wl, torch, device, stream, hbm, steps=SWEEP_STEPS):
 def cpu_baseline_leg(ctap, wl, torch, device, stream, seconds_cap=30.0, sweep=True):
     """The FP64 oracle, as it stands, on the host cores.  Timed: split steps
     of the full 256x256x1024 workload, as many as fit in about
-    `seconds_cap`.  The oracle's own results then anchor the GPU paths: the
+    `seconds_cap`; the oracle's seconds per step at every sweep point (its 3
+    parity steps; 100 more at the grids of at most 128^3), and on one thread
+    at 128^3.  The oracle's own results then anchor the GPU paths: the
     relative L2 of the complex64 and complex128 states after the same steps
-    from the same psi0, and after 2 steps at every sweep point."""
+    from the same psi0, and after 3 steps at every sweep point."""
     import oracle
     box = wl.CTAP_BOX
     z = wl.axis(SHAPE[0], box[4], box[5])
@@ -621,15 +623,29 @@ def cpu_baseline_leg(ctap, wl, torch, device, stream, seconds_cap=30.0, sweep=Tr
                 else:
                     cz = wl.guide_centres(wl.axis(shape[0], sbox[4], sbox[5]))
                     Vs = oracle.ctap_potential(shape, sbox, wl.V0, wl.SIGMA_GUIDE, cz[0], cz[2])
-                r = torch.from_numpy(oracle.step(p0, Vs, sbox, SWEEP_DT, 2)).to(device)
+                t0 = time.perf_counter()
+                r = torch.from_numpy(oracle.step(p0, Vs, sbox, SWEEP_DT, 3)).to(device)
+                row = {"grid": list(shape[::-1]), "potential": potential, "steps": 3,
+                       "oracle_s_per_step": (time.perf_counter() - t0) / 3,
+                       "oracle_threads": oracle.num_threads()}
+                if np.prod(shape) <= 128 ** 3:
+                    t0 = time.perf_counter()
+                    oracle.step(p0, Vs, sbox, SWEEP_DT, 100)
+                    row["oracle_s_per_step_100"] = (time.perf_counter() - t0) / 100
+                if np.prod(shape) == 128 ** 3 and potential == "ctap":
+                    cores = oracle.num_threads()
+                    oracle.set_num_threads(1)
+                    t0 = time.perf_counter()
+                    oracle.step(p0, Vs, sbox, SWEEP_DT, 3)
+                    row["oracle_s_per_step_1_thread"] = (time.perf_counter() - t0) / 3
+                    oracle.set_num_threads(cores)
                 del Vs
-                row = {"grid": list(shape[::-1]), "potential": potential, "steps": 2}
                 for dtype, t in (("c64", torch.complex64), ("c128", torch.complex128)):
                     plan = ctap.Plan(shape, sbox, dtype, stream=stream)
                     setup(plan)
                     g = torch.from_numpy(p0).to(device, t)
                     with torch.cuda.stream(stream):
-                        plan.step(g, 2, SWEEP_DT)
+                        plan.step(g, 3, SWEEP_DT)
                     torch.cuda.synchronize()
                     row[dtype] = rel_l2(torch, g, r)
                     plan.close()

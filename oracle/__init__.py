@@ -53,6 +53,7 @@ def _load():
         lib.orc_wire_field.argtypes = [_dp, ctypes.c_long, ctypes.c_int, _dp, _dp,
                                        ctypes.c_double, _dp]
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -84,6 +85,12 @@ def _check(rc, what):
 def num_threads():
     """OpenMP threads the oracle uses (all host cores unless OMP_NUM_THREADS)."""
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n):
+    """OpenMP threads for the following oracle calls (timing only; the
+    results do not depend on it: every parallel loop runs independent lines)."""
+    _load().orc_set_num_threads(int(n))
 
 
 # ------------------------------------------------------------------ grids

@@ -68,6 +68,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the following calls (omp_set_num_threads): the timed CPU
+ * baseline measures the oracle on one thread as well as on all host cores. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 /* ---------------------------------------------------------- radix-2 FFT */
 
 static int is_pow2(long n) { return n >= 1 && (n & (n - 1)) == 0; }

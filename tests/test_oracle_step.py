@@ -161,3 +161,20 @@ def test_time_reversibility(orc):
 def test_zero_steps_is_identity(orc):
     psi0, V, box = _ctap_case((8, 8, 8))
     assert np.array_equal(orc.step(psi0, V, box, 0.01, 0), psi0)
+
+
+def test_thread_count_does_not_change_results(orc):
+    """The parallel loops of the oracle run independent lines, so one thread
+    and all host cores give bitwise the same state (the timed CPU baseline
+    uses both)."""
+    psi0, V, box = _ctap_case()
+    cores = orc.num_threads()
+    many = orc.step(psi0, V, box, 0.01, 5)
+    orc.set_num_threads(1)
+    try:
+        assert orc.num_threads() == 1
+        one = orc.step(psi0, V, box, 0.01, 5)
+    finally:
+        orc.set_num_threads(cores)
+    assert orc.num_threads() == cores
+    assert np.array_equal(one, many)
