@@ -132,6 +132,33 @@ template <int R, int J> struct RegTw {
     static constexpr double u = ce_sin(phi);
 };
 
+// Complex sum and difference of the butterflies.  Double-float: both
+// components at once in FP32-pair instructions (bitwise the scalar result,
+// half the instructions).
+template <class T> __device__ __forceinline__ Cx<T> cx_add(const Cx<T> &a, const Cx<T> &b)
+{
+    Cx<T> r;
+    r.x = a.x + b.x;
+    r.y = a.y + b.y;
+    return r;
+}
+template <class T> __device__ __forceinline__ Cx<T> cx_sub(const Cx<T> &a, const Cx<T> &b)
+{
+    Cx<T> r;
+    r.x = a.x - b.x;
+    r.y = a.y - b.y;
+    return r;
+}
+template <bool SUB> __device__ __forceinline__ df2 cx_addsub_df(const df2 &a, const df2 &b)
+{
+    float2 zh, zl;
+    dfw::dw_add2<SUB>(make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo),
+                      make_float2(b.x.hi, b.y.hi), make_float2(b.x.lo, b.y.lo), zh, zl);
+    return df2{df(zh.x, zl.x), df(zh.y, zl.y)};
+}
+template <> __device__ __forceinline__ df2 cx_add<df>(const df2 &a, const df2 &b) { return cx_addsub_df<false>(a, b); }
+template <> __device__ __forceinline__ df2 cx_sub<df>(const df2 &a, const df2 &b) { return cx_addsub_df<true>(a, b); }
+
 // Forward R-point DFT (exp(-2 pi i jk/R)) of v[OFF + k*ST], in place; output
 // frequency k lands in register OFF + brev(k, R)*ST.
 template <int R, int OFF, int ST, class T> __device__ __forceinline__ void dft_fwd(Cx<T> *v)
@@ -141,12 +168,9 @@ template <int R, int OFF, int ST, class T> __device__ __forceinline__ void dft_f
         sfor<H>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
             using W = RegTw<R, j>;
-            Cx<T> a = v[OFF + j * ST], b = v[OFF + (j + H) * ST];
-            v[OFF + j * ST].x = a.x + b.x;
-            v[OFF + j * ST].y = a.y + b.y;
-            Cx<T> d;
-            d.x = a.x - b.x;
-            d.y = a.y - b.y;
+            const Cx<T> a = v[OFF + j * ST], b = v[OFF + (j + H) * ST];
+            v[OFF + j * ST] = cx_add<T>(a, b);
+            Cx<T> d = cx_sub<T>(a, b);
             if constexpr (W::mode == 1 || W::mode == 3) rot_f<T>(d, T(W::p), T(W::u));
             if constexpr (W::mode >= 2) { T t = d.x; d.x = d.y; d.y = -t; }   // times -i
             v[OFF + (j + H) * ST] = d;
@@ -170,10 +194,8 @@ template <int R, int OFF, int ST, class T> __device__ __forceinline__ void dft_i
             Cx<T> a = v[OFF + j * ST], d = v[OFF + (j + H) * ST];
             if constexpr (W::mode >= 2) { T t = d.x; d.x = -d.y; d.y = t; }  // times +i
             if constexpr (W::mode == 1 || W::mode == 3) rot_b<T>(d, T(W::p), T(W::u));
-            v[OFF + j * ST].x = a.x + d.x;
-            v[OFF + j * ST].y = a.y + d.y;
-            v[OFF + (j + H) * ST].x = a.x - d.x;
-            v[OFF + (j + H) * ST].y = a.y - d.y;
+            v[OFF + j * ST] = cx_add<T>(a, d);
+            v[OFF + (j + H) * ST] = cx_sub<T>(a, d);
         });
     }
 }

@@ -58,6 +58,60 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
     e = __fmaf_rn(a, b, -p);
 }
 
+// The same on PAIRS of independent values (the real and the imaginary part
+// of one complex value) with the FP32-pair instructions of the sm_100
+// family: element by element the same IEEE round-to-nearest operations in
+// the same order, so the results are bitwise those of the scalar forms.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = padd(a, b);
+    const float2 bb = psub(s, a);
+    e = padd(psub(a, psub(s, bb)), psub(b, bb));
+}
+// two_sum(a, -b) without forming -b: (-b) - bb = -(b + bb) exactly, and
+// x + (-y) rounds as x - y
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = psub(a, b);
+    const float2 bb = psub(s, a);
+    e = psub(psub(a, psub(s, bb)), padd(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = padd(a, b);
+    e = psub(b, psub(s, a));
+}
+// DWPlusDW on pairs (SUB: the second operand negated), hi and lo parts
+template <bool SUB>
+__device__ __forceinline__ void dw_add2(float2 xh, float2 xl, float2 yh, float2 yl, float2 &zh, float2 &zl)
+{
+    float2 sh, sl, th, tl, vh, vl;
+    if constexpr (SUB) {
+        two_diff2(xh, yh, sh, sl);
+        two_diff2(xl, yl, th, tl);
+    } else {
+        two_sum2(xh, yh, sh, sl);
+        two_sum2(xl, yl, th, tl);
+    }
+    const float2 c = padd(sl, th);
+    fast_two_sum2(sh, c, vh, vl);
+    const float2 w = padd(tl, vl);
+    fast_two_sum2(vh, w, zh, zl);
+}
+
 }  // namespace dfw
 
 __device__ __forceinline__ df operator+(df x, df y)
