@@ -159,11 +159,108 @@ template <bool SUB> __device__ __forceinline__ df2 cx_addsub_df(const df2 &a, co
 template <> __device__ __forceinline__ df2 cx_add<df>(const df2 &a, const df2 &b) { return cx_addsub_df<false>(a, b); }
 template <> __device__ __forceinline__ df2 cx_sub<df>(const df2 &a, const df2 &b) { return cx_addsub_df<true>(a, b); }
 
+// Two double-float complex values rotated at once (the x parts as one pair,
+// the y parts as another): a by the lifting pair (pa, ua), b by (pb, ub);
+// BACK: the exact mirror (rot_b).  Element by element the operations of
+// rot_f / rot_b, so bitwise their results.
+// (P, U: the coefficient pairs, already negated for the mirror)
+__device__ __forceinline__ void rot2_dfp(df2 &a, df2 &b, const dfp &P, const dfp &U)
+{
+    dfp X{make_float2(a.x.hi, b.x.hi), make_float2(a.x.lo, b.x.lo)};
+    dfp Y{make_float2(a.y.hi, b.y.hi), make_float2(a.y.lo, b.y.lo)};
+    X = fmadd2(P, Y, X);
+    Y = fmadd2(U, X, Y);
+    X = fmadd2(P, Y, X);
+    a.x = df(X.h.x, X.l.x);
+    b.x = df(X.h.y, X.l.y);
+    a.y = df(Y.h.x, Y.l.x);
+    b.y = df(Y.h.y, Y.l.y);
+}
+template <bool BACK>
+__device__ __forceinline__ void rot2_df(df2 &a, df2 &b, const df &pa, const df &ua, const df &pb, const df &ub)
+{
+    const float sg = BACK ? -1.0f : 1.0f;          // exact negation of the coefficients
+    const dfp P{make_float2(sg * pa.hi, sg * pb.hi), make_float2(sg * pa.lo, sg * pb.lo)};
+    const dfp U{make_float2(sg * ua.hi, sg * ub.hi), make_float2(sg * ua.lo, sg * ub.lo)};
+    rot2_dfp(a, b, P, U);
+}
+// lift_f / lift_b of two double-float values at once (bitwise the single forms)
+__device__ __forceinline__ void lift2_f(df2 &a, df2 &b, const Lift<df> &wa, const Lift<df> &wb)
+{
+    rot2_df<false>(a, b, wa.p, wa.u, wb.p, wb.u);
+    a.x = sign_mul(a.x, wa.s);
+    a.y = sign_mul(a.y, wa.s);
+    b.x = sign_mul(b.x, wb.s);
+    b.y = sign_mul(b.y, wb.s);
+}
+__device__ __forceinline__ void lift2_b(df2 &a, df2 &b, const Lift<df> &wa, const Lift<df> &wb)
+{
+    a.x = sign_mul(a.x, wa.s);
+    a.y = sign_mul(a.y, wa.s);
+    b.x = sign_mul(b.x, wb.s);
+    b.y = sign_mul(b.y, wb.s);
+    rot2_df<true>(a, b, wa.p, wa.u, wb.p, wb.u);
+}
+// lift_f / lift_b of two values, each with its own twiddle (double-float:
+// both at once; otherwise one after the other)
+template <class T>
+__device__ __forceinline__ void lift_pair_f(Cx<T> &a, Cx<T> &b, const Lift<T> &wa, const Lift<T> &wb)
+{
+    if constexpr (std::is_same<T, df>::value) {
+        lift2_f(a, b, wa, wb);
+    } else {
+        lift_f<T>(a, wa);
+        lift_f<T>(b, wb);
+    }
+}
+template <class T>
+__device__ __forceinline__ void lift_pair_b(Cx<T> &a, Cx<T> &b, const Lift<T> &wa, const Lift<T> &wb)
+{
+    if constexpr (std::is_same<T, df>::value) {
+        lift2_b(a, b, wa, wb);
+    } else {
+        lift_b<T>(a, wa);
+        lift_b<T>(b, wb);
+    }
+}
+// both components of a double-float complex value times s (x *= s, y *= s)
+__device__ __forceinline__ void cx_scale_df(df2 &v, const df &s)
+{
+    float2 zh, zl;
+    dfw::dw_mul2(make_float2(v.x.hi, v.y.hi), make_float2(v.x.lo, v.y.lo), make_float2(s.hi, s.hi),
+                 make_float2(s.lo, s.lo), zh, zl);
+    v.x = df(zh.x, zl.x);
+    v.y = df(zh.y, zl.y);
+}
+
 // Forward R-point DFT (exp(-2 pi i jk/R)) of v[OFF + k*ST], in place; output
 // frequency k lands in register OFF + brev(k, R)*ST.
 template <int R, int OFF, int ST, class T> __device__ __forceinline__ void dft_fwd(Cx<T> *v)
 {
-    if constexpr (R > 1) {
+    if constexpr (std::is_same<T, df>::value && R >= 4) {
+        // double-float: the same butterflies with the rotations of levels j
+        // and j + R/4 (one angle; the second then times -i) done as pairs
+        constexpr int H = R / 2, Q4 = R / 4;
+        sfor<H>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const Cx<T> a = v[OFF + j * ST], b = v[OFF + (j + H) * ST];
+            v[OFF + j * ST] = cx_add<T>(a, b);
+            v[OFF + (j + H) * ST] = cx_sub<T>(a, b);
+        });
+        sfor<Q4>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            using W = RegTw<R, j>;
+            static_assert(RegTw<R, j + Q4>::mode == (j == 0 ? 2 : 3), "paired levels");
+            Cx<T> &d1 = v[OFF + (j + H) * ST];
+            Cx<T> &d2 = v[OFF + (j + Q4 + H) * ST];
+            if constexpr (W::mode == 1) rot2_df<false>(d1, d2, T(W::p), T(W::u), T(W::p), T(W::u));
+            T t = d2.x;                                 // times -i
+            d2.x = d2.y;
+            d2.y = -t;
+        });
+        dft_fwd<H, OFF, ST, T>(v);
+        dft_fwd<H, OFF + H * ST, ST, T>(v);
+    } else if constexpr (R > 1) {
         constexpr int H = R / 2;
         sfor<H>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
@@ -184,7 +281,27 @@ template <int R, int OFF, int ST, class T> __device__ __forceinline__ void dft_f
 // natural, R times the inverse DFT.
 template <int R, int OFF, int ST, class T> __device__ __forceinline__ void dft_inv(Cx<T> *v)
 {
-    if constexpr (R > 1) {
+    if constexpr (std::is_same<T, df>::value && R >= 4) {
+        constexpr int H = R / 2, Q4 = R / 4;
+        dft_inv<H, OFF, ST, T>(v);
+        dft_inv<H, OFF + H * ST, ST, T>(v);
+        sfor<Q4>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            using W = RegTw<R, j>;
+            Cx<T> &d1 = v[OFF + (j + H) * ST];
+            Cx<T> &d2 = v[OFF + (j + Q4 + H) * ST];
+            T t = d2.x;                                 // times +i
+            d2.x = -d2.y;
+            d2.y = t;
+            if constexpr (W::mode == 1) rot2_df<true>(d1, d2, T(W::p), T(W::u), T(W::p), T(W::u));
+        });
+        sfor<H>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const Cx<T> a = v[OFF + j * ST], d = v[OFF + (j + H) * ST];
+            v[OFF + j * ST] = cx_add<T>(a, d);
+            v[OFF + (j + H) * ST] = cx_sub<T>(a, d);
+        });
+    } else if constexpr (R > 1) {
         constexpr int H = R / 2;
         dft_inv<H, OFF, ST, T>(v);
         dft_inv<H, OFF + H * ST, ST, T>(v);
@@ -413,6 +530,47 @@ __device__ __forceinline__ void lift_small(df th, df &p, df &u)
     t = fmadd(h2, t, df(1.3333333333333333e-01));
     t = fmadd(h2, t, df(3.3333333333333333e-01));
     p = -fmadd(h2 * h, t, h);
+}
+
+// lift_small for two angles at once (the coefficients as pairs): element by
+// element the operations of lift_small, so bitwise its results
+__device__ __forceinline__ dfp dfp_const(double c)
+{
+    const df d(c);
+    return dfp{make_float2(d.hi, d.hi), make_float2(d.lo, d.lo)};
+}
+__device__ __forceinline__ dfp dfp_mul(const dfp &x, const dfp &y)
+{
+    dfp z;
+    dfw::dw_mul2(x.h, x.l, y.h, y.l, z.h, z.l);
+    return z;
+}
+__device__ __forceinline__ void lift_small2(df th0, df th1, dfp &p, dfp &u)
+{
+    const dfp a{make_float2(-th0.hi, -th1.hi), make_float2(-th0.lo, -th1.lo)};
+    const dfp a2 = dfp_mul(a, a);
+    dfp s = fmadd2(a2, dfp_const(-2.5052108385441720e-08), dfp_const(2.7557319223985893e-06));
+    s = fmadd2(a2, s, dfp_const(-1.9841269841269841e-04));
+    s = fmadd2(a2, s, dfp_const(8.3333333333333333e-03));
+    s = fmadd2(a2, s, dfp_const(-1.6666666666666667e-01));
+    u = fmadd2(dfp_mul(a2, a), s, a);
+    // h = a/2 as mul_f(a, 0.5f) (DWTimesFP)
+    dfp h;
+    {
+        const float2 y = make_float2(0.5f, 0.5f);
+        const float2 ch = dfw::pmul(a.h, y);
+        const float2 cl1 = dfw::pfma(a.h, y, dfw::pneg(ch));
+        const float2 cl3 = dfw::pfma(a.l, y, cl1);
+        dfw::fast_two_sum2(ch, cl3, h.h, h.l);
+    }
+    const dfp h2 = dfp_mul(h, h);
+    dfp t = fmadd2(h2, dfp_const(3.5921280365724810e-03), dfp_const(8.8632355299021966e-03));
+    t = fmadd2(h2, t, dfp_const(2.1869488536155203e-02));
+    t = fmadd2(h2, t, dfp_const(5.3968253968253968e-02));
+    t = fmadd2(h2, t, dfp_const(1.3333333333333333e-01));
+    t = fmadd2(h2, t, dfp_const(3.3333333333333333e-01));
+    const dfp q = fmadd2(dfp_mul(h2, h), t, h);
+    p = dfp{dfw::pneg(q.h), dfw::pneg(q.l)};
 }
 
 // double-float angle: reduced and evaluated in FP64 (kicks use the

@@ -112,7 +112,35 @@ __device__ __forceinline__ void dw_add2(float2 xh, float2 xl, float2 yh, float2 
     fast_two_sum2(vh, w, zh, zl);
 }
 
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pneg(float2 a) { return make_float2(-a.x, -a.y); }
+// DWTimesDW on pairs
+__device__ __forceinline__ void dw_mul2(float2 xh, float2 xl, float2 yh, float2 yl, float2 &zh, float2 &zl)
+{
+    const float2 ch = pmul(xh, yh);
+    const float2 cl1 = pfma(xh, yh, pneg(ch));
+    const float2 tl0 = pmul(xl, yl);
+    const float2 tl1 = pfma(xh, yl, tl0);
+    const float2 cl2 = pfma(xl, yh, tl1);
+    const float2 cl3 = padd(cl1, cl2);
+    fast_two_sum2(ch, cl3, zh, zl);
+}
+
 }  // namespace dfw
+
+// a pair of double-float values (two lanes of FP32 pairs): hi parts, lo parts
+struct dfp {
+    float2 h, l;
+};
+// a b + c on pairs (the product, then the sum: as fmadd on each element)
+__device__ __forceinline__ dfp fmadd2(const dfp &a, const dfp &b, const dfp &c)
+{
+    dfp t, z;
+    dfw::dw_mul2(a.h, a.l, b.h, b.l, t.h, t.l);
+    dfw::dw_add2<false>(t.h, t.l, c.h, c.l, z.h, z.l);
+    return z;
+}
 
 __device__ __forceinline__ df operator+(df x, df y)
 {

@@ -142,6 +142,19 @@ __device__ __forceinline__ void kick_rt(df2 &v, df th, int small)
     v.x = sign_mul(v.x, s);
     v.y = sign_mul(v.y, s);
 }
+// two kicks at once when both angles take the short series (bitwise
+// kick_rt on each; otherwise kick_rt on each)
+__device__ __forceinline__ void kick_rt2(df2 &v0, df2 &v1, df th0, df th1, int small)
+{
+    if (small && fabsf(th0.hi) <= 0.1f && fabsf(th1.hi) <= 0.1f) {
+        dfp p, u;
+        lift_small2(th0, th1, p, u);
+        rot2_dfp(v0, v1, p, u);
+        return;
+    }
+    kick_rt(v0, th0, small);
+    kick_rt(v1, th1, small);
+}
 __device__ __forceinline__ void ld2(const df2 *p, df2 &a, df2 &b)
 {
     a = p[0];
@@ -370,7 +383,9 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                     const int j = q % RA, row = q / RA;
                     dft_inv<RB, 0, 1, T>(v[i]);
 #pragma unroll
-                    for (int rr = 1; rr < RB; ++rr) lift_b<T>(v[i][rr], wx[rr * RA + j]);
+                    for (int rr = 1; rr + 1 < RB; rr += 2)
+                        lift_pair_b<T>(v[i][rr], v[i][rr + 1], wx[rr * RA + j], wx[(rr + 1) * RA + j]);
+                    lift_b<T>(v[i][RB - 1], wx[(RB - 1) * RA + j]);
 #pragma unroll
                     for (int rr = 0; rr < RB; ++rr) sm[row * PITCH + j + RA * rr] = v[i][rr];
                 }
@@ -402,8 +417,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
 #pragma unroll
             for (int rr = 1; rr < YB; ++rr) {
                 const Lift<T> tw = wy[i * rr];
-                lift_b<T>(v[rr], tw);
-                lift_b<T>(w[rr], tw);
+                lift_pair_b<T>(v[rr], w[rr], tw, tw);
             }
 #pragma unroll
             for (int rr = 0; rr < YB; ++rr) st2(sm + (i + YA * rr) * PITCH + p, v[rr], w[rr]);
@@ -535,8 +549,16 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                 if (HOT) {
                     const T hx = htab[p];
                     const int tier = a.small_angle;     // 1 or 2 (uniform across the grid)
+                    if constexpr (std::is_same<T, df>::value && YA % 2 == 0) {
+                        // double-float: two rows per kick (pairs of FP32 pairs)
 #pragma unroll
-                    for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], fmadd(gtab[i + YB * rr], hx, thz), tier);
+                        for (int rr = 0; rr < YA; rr += 2)
+                            kick_rt2(v[c][rr], v[c][rr + 1], fmadd(gtab[i + YB * rr], hx, thz),
+                                     fmadd(gtab[i + YB * (rr + 1)], hx, thz), tier);
+                    } else {
+#pragma unroll
+                        for (int rr = 0; rr < YA; ++rr) kick_rt(v[c][rr], fmadd(gtab[i + YB * rr], hx, thz), tier);
+                    }
                     // (the hot variant is only chosen when the short series applies)
                 } else if (kick) {
                     // norm partial of the column in the element type (FP32 for complex64)
@@ -563,29 +585,35 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
                     } else {
                         const int small = a.small_angle;
                         const T hx = (k.form == VF_PRODUCT) ? htab[p] : T(0);
+                        auto angle = [&](int rr) -> T {
+                            const int jy = i + YB * rr;
+                            return (k.form == VF_PRODUCT)
+                                       ? fmadd(gtab[jy], hx, thz)
+                                       : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
+                        };
+                        // double-float real time: two rows per kick (pairs of FP32 pairs)
+                        auto kick_rows = [&]() {
+                            if constexpr (std::is_same<T, df>::value && YA % 2 == 0) {
+                                if (!k.imag) {
+#pragma unroll
+                                    for (int rr = 0; rr < YA; rr += 2)
+                                        kick_rt2(v[c][rr], v[c][rr + 1], angle(rr), angle(rr + 1), small);
+                                    return;
+                                }
+                            }
+#pragma unroll
+                            for (int rr = 0; rr < YA; ++rr) kick_one<T>(v[c][rr], angle(rr), k.imag, small);
+                        };
+                        kick_rows();
 #pragma unroll
                         for (int rr = 0; rr < YA; ++rr) {
                             const int jy = i + YB * rr;
-                            const T th =
-                                (k.form == VF_PRODUCT)
-                                    ? fmadd(gtab[jy], hx, thz)
-                                    : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
-                            kick_one<T>(v[c][rr], th, k.imag, small);
                             if (flags & XY_RED_NORM) nrm += norm2(v[c][rr]);
                             if (flags & XY_STATE_OUT)
                                 a.state_out[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] = v[c][rr];
                         }
                         if (flags & XY_GRAD) grad_task(v[c], i, x);
-                        if (flags & XY_KICK_SPLIT) {
-#pragma unroll
-                            for (int rr = 0; rr < YA; ++rr) {
-                                const int jy = i + YB * rr;
-                                const T th = (k.form == VF_PRODUCT)
-                                                 ? fmadd(gtab[jy], hx, thz)
-                                                 : k.Vd[pbase + ((long long)(r + jy * g.P) << g.lgnx) + x] * tau;
-                                kick_one<T>(v[c][rr], th, k.imag, small);
-                            }
-                        }
+                        if (flags & XY_KICK_SPLIT) kick_rows();
                     }
                     if (flags & XY_RED_NORM) acc[0] += (double)nrm;
                 }
@@ -631,8 +659,7 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
 #pragma unroll
             for (int rr = 1; rr < YB; ++rr) {
                 const Lift<T> tw = wy[i * rr];
-                lift_f<T>(v[rr], tw);
-                lift_f<T>(w[rr], tw);
+                lift_pair_f<T>(v[rr], w[rr], tw, tw);
             }
             dft_fwd<YB, 0, 1, T>(v);
             dft_fwd<YB, 0, 1, T>(w);
@@ -661,7 +688,9 @@ __global__ void __launch_bounds__(xy_threads<T, HOT>()) xy_fast_kernel(const XYA
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) v[rr] = sm[row * PITCH + j + RA * rr];
 #pragma unroll
-            for (int rr = 1; rr < RB; ++rr) lift_f<T>(v[rr], wx[rr * RA + j]);
+            for (int rr = 1; rr + 1 < RB; rr += 2)
+                lift_pair_f<T>(v[rr], v[rr + 1], wx[rr * RA + j], wx[(rr + 1) * RA + j]);
+            lift_f<T>(v[RB - 1], wx[(RB - 1) * RA + j]);
             dft_fwd<RB, 0, 1, T>(v);
             C2 *rowp = dst + ((long long)(row * g.P + r) << g.lgnx);
             sfor<RB>([&](auto kc) {

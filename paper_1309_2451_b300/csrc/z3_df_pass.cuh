@@ -95,8 +95,10 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
         for (int i = 0; i < Q; ++i) {
             const int q = t + i * NT;
             const int xo = q % W, zz = q / W;
+            // the lifted rotations in pairs (bitwise the single forms)
 #pragma unroll
-            for (int rr = 1; rr < P; ++rr) lift_f<T>(v[i][rr], cw[rr]);
+            for (int rr = 1; rr + 1 < P; rr += 2) lift2_f(v[i][rr], v[i][rr + 1], cw[rr], cw[rr + 1]);
+            lift_f<T>(v[i][P - 1], cw[P - 1]);
             dft_fwd<P, 0, 1, T>(v[i]);
             sfor<P>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
@@ -127,10 +129,10 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
         const int base = n3 + N2 * k1;
         C2 v[ZM];
 #pragma unroll
-        for (int n2 = 0; n2 < ZM; ++n2) {
-            v[n2] = sm[at(base + ZB * n2, col)];
-            lift_f<T>(v[n2], wz[(ZB * n2 + n3) * k1]);
-        }
+        for (int n2 = 0; n2 < ZM; ++n2) v[n2] = sm[at(base + ZB * n2, col)];
+#pragma unroll
+        for (int n2 = 0; n2 < ZM; n2 += 2)
+            lift2_f(v[n2], v[n2 + 1], wz[(ZB * n2 + n3) * k1], wz[(ZB * (n2 + 1) + n3) * k1]);
         dft_fwd<ZM, 0, 1, T>(v);
         sfor<ZM>([&](auto kc) {
             constexpr int k2 = decltype(kc)::value;
@@ -152,39 +154,41 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
             C2 v[ZB];
 #pragma unroll
             for (int j = 0; j < ZB; ++j) v[j] = sm[at(base + j, col)];
-            sfor<ZB - 1>([&](auto jc) {
-                constexpr int j = decltype(jc)::value + 1;
-                if constexpr (j % 4 == 0) hoist_fence();
-                lift_f<T>(v[j], wz[ZA * j * k2]);
+            sfor<(ZB - 1) / 2>([&](auto jc) {
+                constexpr int j = 2 * decltype(jc)::value + 1;
+                if constexpr (j % 4 == 1) hoist_fence();
+                lift2_f(v[j], v[j + 1], wz[ZA * j * k2], wz[ZA * (j + 1) * k2]);
             });
+            lift_f<T>(v[ZB - 1], wz[ZA * (ZB - 1) * k2]);
             dft_fwd<ZB, 0, 1, T>(v);
             // register brev(k3) holds kz = k1 + ZA k2 + ZA ZM k3
             const int kzb = k1 + ZA * k2;
             const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky];
-            sfor<ZB>([&](auto kc) {
-                constexpr int k3 = decltype(kc)::value;
+            // two frequencies at a time: the three rotations as pairs, the
+            // scale on both components at once
+            sfor<ZB / 2>([&](auto kc) {
+                constexpr int k3 = 2 * decltype(kc)::value;
                 if constexpr (k3 % 4 == 0) hoist_fence();
-                C2 &u = v[brev(k3, ZB)];
-                const Lift<T> az = kz[kzb + ZA * ZM * k3];
+                C2 &u0 = v[brev(k3, ZB)], &u1 = v[brev(k3 + 1, ZB)];
+                const Lift<T> az0 = kz[kzb + ZA * ZM * k3], az1 = kz[kzb + ZA * ZM * (k3 + 1)];
                 if (a.imag) {
-                    const T f = ax.f * ay.f * az.f * sc;
-                    u.x *= f;
-                    u.y *= f;
+                    cx_scale_df(u0, ax.f * ay.f * az0.f * sc);
+                    cx_scale_df(u1, ax.f * ay.f * az1.f * sc);
                 } else {
-                    rot_f<T>(u, ax.p, ax.u);
-                    rot_f<T>(u, ay.p, ay.u);
-                    rot_f<T>(u, az.p, az.u);
-                    const T s = ax.s * ay.s * az.s * sc;
-                    u.x *= s;
-                    u.y *= s;
+                    rot2_df<false>(u0, u1, ax.p, ax.u, ax.p, ax.u);
+                    rot2_df<false>(u0, u1, ay.p, ay.u, ay.p, ay.u);
+                    rot2_df<false>(u0, u1, az0.p, az0.u, az1.p, az1.u);
+                    cx_scale_df(u0, ax.s * ay.s * az0.s * sc);
+                    cx_scale_df(u1, ax.s * ay.s * az1.s * sc);
                 }
             });
             dft_inv<ZB, 0, 1, T>(v);
-            sfor<ZB - 1>([&](auto jc) {
-                constexpr int j = decltype(jc)::value + 1;
-                if constexpr (j % 4 == 0) hoist_fence();
-                lift_b<T>(v[j], wz[ZA * j * k2]);
+            sfor<(ZB - 1) / 2>([&](auto jc) {
+                constexpr int j = 2 * decltype(jc)::value + 1;
+                if constexpr (j % 4 == 1) hoist_fence();
+                lift2_b(v[j], v[j + 1], wz[ZA * j * k2], wz[ZA * (j + 1) * k2]);
             });
+            lift_b<T>(v[ZB - 1], wz[ZA * (ZB - 1) * k2]);
 #pragma unroll
             for (int j = 0; j < ZB; ++j) sm[at(base + j, col)] = v[j];
         }
@@ -203,10 +207,10 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
         });
         dft_inv<ZM, 0, 1, T>(v);
 #pragma unroll
-        for (int n2 = 0; n2 < ZM; ++n2) {
-            lift_b<T>(v[n2], wz[(ZB * n2 + n3) * k1]);
-            sm[at(base + ZB * n2, col)] = v[n2];
-        }
+        for (int n2 = 0; n2 < ZM; n2 += 2)
+            lift2_b(v[n2], v[n2 + 1], wz[(ZB * n2 + n3) * k1], wz[(ZB * (n2 + 1) + n3) * k1]);
+#pragma unroll
+        for (int n2 = 0; n2 < ZM; ++n2) sm[at(base + ZB * n2, col)] = v[n2];
     }
     __syncthreads();
 
@@ -234,7 +238,8 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
         });
         dft_inv<P, 0, 1, T>(v);
 #pragma unroll
-        for (int rr = 1; rr < P; ++rr) lift_b<T>(v[rr], cw[rr]);
+        for (int rr = 1; rr + 1 < P; rr += 2) lift2_b(v[rr], v[rr + 1], cw[rr], cw[rr + 1]);
+        lift_b<T>(v[P - 1], cw[P - 1]);
         C2 *p = a.dst + (long long)zz * g.plane + colbase + xo;
 #pragma unroll
         for (int rr = 0; rr < P; ++rr) st_stream(p + ((long long)rr << g.lgnx), v[rr]);
