@@ -317,6 +317,20 @@ def test_double_float_three_stage_z_pass(ctap, shape, row_classes, steps):
     assert np.allclose(got, want, rtol=1e-11, atol=1e-14)
 
 
+def test_double_float_three_stage_z_pass_imaginary_time(ctap):
+    """Imaginary time through the three-stage double-float Z pass (the decay
+    factors of the kinetic step with the per-step renormalisation scale
+    folded in): guides, 1024-point z-lines, against the oracle."""
+    shape, box = (1024, 64, 256), wl.CTAP_BOX
+    plan, V, c = guides(ctap, shape, box, "c128df")
+    assert plan.info()["fast_mask"] & 2, plan.info()
+    psi0 = guide_state(shape, box, 44)
+    psi = to_dev(psi0, "c128")
+    plan.step(psi, 10, 0.01, imag=True)
+    ref = oracle.step(psi0, V, box, 0.01, 10, imag=True)
+    assert rel(psi.cpu().numpy(), ref) < 1e-12
+
+
 def test_double_float_imaginary_time(ctap):
     shape, box = (32, 32, 32), (-8.0, 8.0, -8.0, 8.0, -8.0, 8.0)
     vx, vy, vz = wl.harmonic_parts(shape, box)
