@@ -203,7 +203,10 @@ ctap_status get_tables(PlanState &st, double dt, int imag, TabSet **out)
         std::vector<unsigned char> h;
         build_kinetic(st, dt, imag, h);
         CTAP_TRY(upload(st, &hit->kin, nullptr, h.data(), h.size()));
-        if (packed_z_on(st) && !imag) {
+        // the (kx, ky) kinetic rotation of each column as one table entry:
+        // the packed complex64 Z pass and the double-float three-stage one
+        const bool df_z3 = st.dtype == CTAP_C128_DF && st.fast_z && st.nz == 1024;
+        if ((packed_z_on(st) || df_z3) && !imag) {
             build_kinetic_xy(st, dt, h);
             CTAP_TRY(upload(st, &hit->kin_xy, nullptr, h.data(), h.size()));
         }

@@ -23,7 +23,7 @@ struct TabSet {
     void *kin;
     void *sep;
     bool sep_valid;
-    void *kin_xy = nullptr;        // complex64 real time: (kx, ky) rotations [ny][nx] (packed Z pass)
+    void *kin_xy = nullptr;        // real time: (kx, ky) rotations [ny][nx], plan element type (packed complex64 and double-float three-stage Z passes)
 };
 
 // an instantiated CUDA graph of one ctap_step call

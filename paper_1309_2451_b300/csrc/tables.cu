@@ -205,14 +205,14 @@ void build_kinetic(const PlanState &p, double dt, int imag, std::vector<unsigned
 
 void build_kinetic_xy(const PlanState &p, double dt, std::vector<unsigned char> &host)
 {
-    host.assign((size_t)p.nx * p.ny * sizeof(Lift<float>), 0);
+    host.assign((size_t)p.nx * p.ny * lift_size(p), 0);
     for (int my = 0; my < p.ny; ++my) {
         const double ky = wavenumber(my, p.ny, p.box[2], p.box[3]);
         for (int mx = 0; mx < p.nx; ++mx) {
             const double kx = wavenumber(mx, p.nx, p.box[0], p.box[1]);
             double pp, u, sg;
             lift_angle(-0.5 * (kx * kx + ky * ky) * dt, pp, u, sg);
-            put<float>(host, (size_t)my * p.nx + mx, pp, u, sg, 1.0);
+            put_any(p, host, (size_t)my * p.nx + mx, pp, u, sg, 1.0);
         }
     }
 }

@@ -41,7 +41,9 @@ __device__ __forceinline__ void hoist_fence() { asm volatile("" ::: "memory"); }
 //   Z2  radix ZA over n1 (rows n2' + ZM ZB n1, n2' = ZB n2 + n3);
 //   Z2b twiddle exp(-2 pi i n2' k1/NZ), radix ZM over n2;
 //   Z3  twiddle exp(-2 pi i n3 k2/(ZM ZB)), radix ZB over the ZB contiguous
-//       rows n3, the kinetic factor of kz, and the exact mirror back;
+//       rows n3, the kinetic factor (real time: the (kx, ky) rotation of the
+//       column from its table entry, then the kz one), and the exact mirror
+//       back;
 //   Z4b, Z4 the mirrors of Z2b and Z2.
 template <class T, int NZ, int ZA, int ZM, int ZB, int P, int W, int NT>
 __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
@@ -164,6 +166,9 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
             // register brev(k3) holds kz = k1 + ZA k2 + ZA ZM k3
             const int kzb = k1 + ZA * k2;
             const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky];
+            // real time: the (kx, ky) rotation as one table entry (FP64 angle)
+            const Lift<T> *kxy = static_cast<const Lift<T> *>(a.kin_xy);
+            const Lift<T> axy = kxy ? kxy[(long long)ky * g.nx + kx] : ax;
             // two frequencies at a time: the three rotations as pairs, the
             // scale on both components at once
             sfor<ZB / 2>([&](auto kc) {
@@ -174,6 +179,11 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
                 if (a.imag) {
                     cx_scale_df(u0, ax.f * ay.f * az0.f * sc);
                     cx_scale_df(u1, ax.f * ay.f * az1.f * sc);
+                } else if (kxy) {
+                    rot2_df<false>(u0, u1, axy.p, axy.u, axy.p, axy.u);
+                    rot2_df<false>(u0, u1, az0.p, az0.u, az1.p, az1.u);
+                    cx_scale_df(u0, axy.s * az0.s * sc);
+                    cx_scale_df(u1, axy.s * az1.s * sc);
                 } else {
                     rot2_df<false>(u0, u1, ax.p, ax.u, ax.p, ax.u);
                     rot2_df<false>(u0, u1, ay.p, ay.u, ay.p, ay.u);
