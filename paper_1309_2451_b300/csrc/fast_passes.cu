@@ -1646,8 +1646,8 @@ bool launch_z_fast(const ZArgs<float> &a, cudaStream_t st)
 // Double-float: the specialised XY pass for 256-point rows (16-point
 // register DFTs) and the three-stage Z pass of z3_df_pass.cuh for
 // 1024-point z-lines (fully unrolled 32-point register DFTs in double-float
-// arithmetic are too large to compile); other z lengths and the
-// observables pass take the generic Z pass.
+// arithmetic are too large to compile); other z lengths take the generic Z
+// pass.
 bool launch_xy_fast(const XYArgs<df> &a, cudaStream_t st)
 {
     return try_xy<df, 256, 16, 16, 32, 4, 8>(a, st);

@@ -6,8 +6,8 @@
 // task per thread fits the 128-register budget of 512 threads.
 // Each (P, W) tile geometry is instantiated in its own translation unit
 // (z3_df_p8.cu, z3_df_p4.cu, z3_df_p2.cu) so that the build compiles them in
-// parallel.  Observables launches (the kinetic-energy sum) take the generic
-// Z pass.
+// parallel.  Observables launches stop after the forward transform with the
+// FP64 kinetic-energy sum (one partial per CTA).
 #pragma once
 
 #include "kernels.cuh"
@@ -30,6 +30,24 @@ __device__ __forceinline__ void st_stream(df2 *p, const df2 &v)
 // compiler-only fence: keeps the twiddle-table loads of a stage from being
 // hoisted en masse
 __device__ __forceinline__ void hoist_fence() { asm volatile("" ::: "memory"); }
+
+// fixed-order sum of one FP64 value over the CTA (warp shuffles, then the
+// warp sums in order by warp 0); thread 0 writes it
+template <int NT> __device__ __forceinline__ void cta_sum(double v, double *out)
+{
+    __shared__ double red[NT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double w = (lane < NT / 32) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        if (lane == 0) *out = w;
+    }
+}
 
 // Z pass with three register stages, NZ = ZA ZM ZB (1024 = 16 x 4 x 16), for
 // complex128-sized elements.  It exists for the double-float path: the
@@ -72,7 +90,7 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
     Lift<T> *kz = wz + NZ;                                      // z kinetic factors
     for (int e = t; e < NZ; e += NT) {
         wz[e] = a.tw[g.fast_z_off + e];
-        kz[e] = a.kin[g.nx + g.ny + e];
+        if (!a.observe) kz[e] = a.kin[g.nx + g.ny + e];
     }
     Lift<T> cw[P];
 #pragma unroll
@@ -147,6 +165,7 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
     // kinetic factor, inverse
     {
         const T sc = a.inv_n * (a.scale ? (T)(*a.scale) : T(1));
+        double acc = 0.0;                              // observables: sum k^2/2 |psi_k|^2
         for (int q = t; q < C * ZA * ZM; q += NT) {
             const int col = q % C, r2 = q / C;
             const int k2 = r2 % ZM, k1 = r2 / ZM;
@@ -165,6 +184,16 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
             dft_fwd<ZB, 0, 1, T>(v);
             // register brev(k3) holds kz = k1 + ZA k2 + ZA ZM k3
             const int kzb = k1 + ZA * k2;
+            if (a.observe) {                           // forward only: the kinetic sum in FP64
+                const double kxy2 = a.k2h[kx] + a.k2h[g.nx + ky];
+                sfor<ZB>([&](auto kc) {
+                    constexpr int k3 = decltype(kc)::value;
+                    const C2 u = v[brev(k3, ZB)];
+                    const double ux = (double)u.x, uy = (double)u.y;
+                    acc += (kxy2 + a.k2h[g.nx + g.ny + kzb + ZA * ZM * k3]) * (ux * ux + uy * uy);
+                });
+                continue;
+            }
             const Lift<T> ax = a.kin[kx], ay = a.kin[g.nx + ky];
             // real time: the (kx, ky) rotation as one table entry (FP64 angle)
             const Lift<T> *kxy = static_cast<const Lift<T> *>(a.kin_xy);
@@ -201,6 +230,10 @@ __global__ void __launch_bounds__(NT, 1) z_fast3_kernel(const ZArgs<T> a)
             lift_b<T>(v[ZB - 1], wz[ZA * (ZB - 1) * k2]);
 #pragma unroll
             for (int j = 0; j < ZB; ++j) sm[at(base + j, col)] = v[j];
+        }
+        if (a.observe) {                               // one partial per CTA, nothing stored
+            cta_sum<NT>(acc, a.partials + blockIdx.x);
+            return;
         }
     }
     __syncthreads();
@@ -266,7 +299,7 @@ constexpr int kZ3NT = 512;
 // launch on the plan's stream when the geometry is this instantiation's
 template <int NZ, int ZA, int ZM, int ZB, int P, int W> bool try_z3(const ZArgs<df> &a, cudaStream_t st)
 {
-    if (a.observe || a.g.nz != NZ || a.g.P != P || a.g.w != W) return false;
+    if (a.g.nz != NZ || a.g.P != P || a.g.w != W) return false;
     const size_t smem = (size_t)NZ * P * W * sizeof(Cx<df>) + 2 * NZ * sizeof(Lift<df>);
     static bool cfg = false;
     if (!cfg) {
