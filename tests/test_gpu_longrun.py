@@ -119,6 +119,30 @@ def test_separable_packed_xy_1000_steps_accuracy_and_norm(ctap):
     assert abs(n1 / n0 - 1.0) < 1e-6
 
 
+def test_double_float_500_steps_against_complex128_full_size(ctap):
+    """The double-float path at the bench size (its specialised XY and
+    three-stage Z passes) for 500 steps from the moving packets: within
+    1e-12 relative L2 of the native complex128 path (whose own error against
+    the oracle is pinned above), norm conserved to the same bound."""
+    shape, box, dt = (1024, 256, 256), wl.CTAP_BOX, 0.0025
+    psi0 = moving_packets(shape, box, seed=27)
+    out, norms = {}, {}
+    for dtype in ("c128", "c128df"):
+        plan, _, _ = guides_plan(ctap, shape, box, dtype)
+        if dtype == "c128df":
+            assert plan.info()["fast_mask"] & 3 == 3, plan.info()
+        psi = to_dev(psi0, "c128")
+        n0 = plan.observables(psi)[0]
+        plan.step(psi, 500, dt)
+        norms[dtype] = plan.observables(psi)[0] / n0 - 1.0
+        out[dtype] = psi
+        plan.close()
+    a, b = out["c128df"], out["c128"]
+    err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    assert err < 1e-12, err
+    assert abs(norms["c128df"]) < 1e-12 and abs(norms["c128"]) < 1e-12, norms
+
+
 # ------------------------------------------------------- C2 end to end
 def c2_initial_state(shape, box):
     """The C2 initial state, prepared by the oracle: the guide-1 transverse
